@@ -1,0 +1,379 @@
+"""Benchmark: 512^3 complex-to-complex 3D FFT on one GB300.
+
+One step is the paper's timing protocol (Section 5: a forward and an inverse
+transform back to back, reported per transform) on a 512^3 complex64 array
+already resident in HBM.  The line also carries the FP16/BF16-storage form of
+the same step (speedup and round-trip error), the roofline of the dominant
+kernel, the same metric end to end through the host-buffer entry point, and
+the FP64 CPU oracle timed on this host's cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wsfft|reference]
+
+Under torchrun (N > 1) every rank runs its own independent transforms
+(replicas: the single-GPU path has no exchange step); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+N_AXIS = 512
+DIMS = (N_AXIS, N_AXIS, N_AXIS)
+ELEMS = N_AXIS ** 3
+FLOPS = 5.0 * ELEMS * math.log2(ELEMS)  # 5 N log2 N (Section 1)
+WORKLOAD = "3D C2C FFT 512x512x512 complex64, forward+inverse per step"
+METRIC = "512^3 C2C 3D FFT us per transform (FFT+IFFT)/2"
+PAPER_CS2_US = 959.3  # Table 1, 512^3 FP32 on a CS-2 (other hardware: context)
+REF_PASSES = 2        # minimum-bytes roofline: 2 passes over the array for 3D
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, v: float) -> float:
+    if world <= 1:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"wsfft_clocks_{os.getpid()}.csv")
+        try:
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            ident = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+        except Exception:
+            ident = str(device_index)
+        self.ident = ident
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.ident, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[3:7]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample_oracle(reps: int = 2):
+    """FP64 CPU oracle on a bounded sample: `reps` forward+inverse pairs of a
+    256^3 transform, scaled to a 512^3 transform by the 5 N log2 N count."""
+    import oracle
+    from paper_2209_15040_gb300 import inputs
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    n = 256
+    x = inputs.complex_input((n, n, n), 1, "normal", "c32").astype(np.complex128)
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        y = oracle.fftn(x, sign=-1)
+        oracle.fftn(y, sign=+1)
+        best = min(best, time.perf_counter() - t0)
+    small_flops = 5.0 * n ** 3 * math.log2(n ** 3)
+    us = best / 2 * (FLOPS / small_flops) * 1e6
+    return {"value": us, "unit": "us per 512^3 transform", "cores": oracle.get_threads(),
+            "kind": "oracle",
+            "sample": f"best of {reps} FP64 forward+inverse pairs at 256^3, "
+                      f"/2 and scaled by 5N log2 N to 512^3"}
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands, on host cores: the reference arm."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2209_15040_gb300 import inputs
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    n = 128
+    x = inputs.complex_input((n, n, n), 1, "normal", "c32").astype(np.complex128)
+    scale = FLOPS / (5.0 * n ** 3 * math.log2(n ** 3))
+    for _ in range(args.warmup):
+        oracle.fftn(oracle.fftn(x, sign=-1), sign=+1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fftn(oracle.fftn(x, sign=-1), sign=+1)
+    dt = time.perf_counter() - t0
+    us = dt / args.steps / 2 * scale * 1e6
+    line = {"metric": METRIC, "value": us, "unit": "us", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "l2": "input larger than L2"},
+            "cpu_baseline": {"value": us, "unit": "us", "cores": oracle.get_threads(),
+                             "kind": "oracle",
+                             "sample": f"each step one FP64 forward+inverse pair at {n}^3, "
+                                       f"/2 and scaled by 5N log2 N to 512^3"},
+            "e2e": {"value": us, "unit": "us", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def timed_pairs(fwd, inv, x, y, steps, warmup, world, stream):
+    for _ in range(warmup):
+        fwd.execute(x.data_ptr(), y.data_ptr(), stream)
+        inv.execute(y.data_ptr(), y.data_ptr(), stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fwd.execute(x.data_ptr(), y.data_ptr(), stream)
+        inv.execute(y.data_ptr(), y.data_ptr(), stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wsfft", choices=["wsfft", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world, rank, local = dist_init()
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    from paper_2209_15040_gb300 import build as _build
+    from paper_2209_15040_gb300 import wsfft as W
+    _build.build_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    hbm_peak, peak_kind = peaks()
+
+    # inputs: N(0,1) re/im, generated on the device (seeded), 1 GiB > L2
+    g = torch.Generator(device=dev)
+    g.manual_seed(1 + rank)
+    x = torch.randn(DIMS + (2,), generator=g, device=dev, dtype=torch.float32)
+    x = torch.view_as_complex(x).contiguous()
+    y = torch.empty_like(x)
+
+    fwd = W.Plan(DIMS, W.C32, W.FORWARD, 1)
+    inv = W.Plan(DIMS, W.C32, W.INVERSE, 1)
+    npass, bytes_exec = fwd.passes()
+    launches_per_step = 2 * npass
+
+    # --- timed region: FP32 pairs, per-launch events on the launching stream
+    clocks = Clocks(local)
+    timed_pairs(fwd, inv, x, y, 0, args.warmup, world, stream)  # warm-up, not recorded
+    fwd.profile(args.steps * npass)
+    inv.profile(args.steps * npass)
+    clocks.start()
+    ms = timed_pairs(fwd, inv, x, y, args.steps, 0, world, stream)
+    clk = clocks.stop()
+    per_launch = fwd.launch_times(args.steps * npass) + inv.launch_times(args.steps * npass)
+    fwd.profile(0)
+    inv.profile(0)
+    ms = allmax(world, ms)
+    ms_per_step = ms / args.steps
+    us_per_transform = ms_per_step * 1e3 / 2 / world  # whole job: world ranks in parallel
+
+    # round-trip error of the FP32 path (paper normalisation: inverse of forward)
+    fwd.execute(x.data_ptr(), y.data_ptr(), stream)
+    inv.execute(y.data_ptr(), y.data_ptr(), stream)
+    torch.cuda.synchronize()
+    rt32 = float(torch.linalg.vector_norm(y - x) / torch.linalg.vector_norm(x))
+
+    # dominant kernel: pass index with the largest mean time
+    pass_ms = [[] for _ in range(npass)]
+    for i, t in enumerate(per_launch):
+        pass_ms[i % npass].append(t)
+    mean_ms = [statistics.mean(v) if v else 0.0 for v in pass_ms]
+    dom = int(np.argmax(mean_ms))
+    bytes_launch = 2 * ELEMS * 8  # one read and one write of the array
+    achieved = bytes_launch / (mean_ms[dom] * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        with open(tr_path) as f:
+            traffic = json.load(f).get("c32_512_pass%d" % dom)
+
+    # --- FP16 / BF16 storage, same step
+    half = {}
+    for name, code, tdt in (("c16f", W.C16F, torch.float16), ("c16bf", W.C16BF, torch.bfloat16)):
+        xh = torch.view_as_real(x).to(tdt).contiguous()
+        yh = torch.empty_like(xh)
+        f16 = W.Plan(DIMS, code, W.FORWARD, 1)
+        i16 = W.Plan(DIMS, code, W.INVERSE, 1)
+        ms16 = allmax(world, timed_pairs(f16, i16, xh, yh, args.steps, args.warmup, world, stream))
+        # forward result vs the FP32 path (orthonormal scaling on both)
+        f16.execute(xh.data_ptr(), yh.data_ptr(), stream)
+        f32o = W.Plan(DIMS, W.C32, W.FORWARD, 1, W.NORM_ORTHO)
+        f32o.execute(x.data_ptr(), y.data_ptr(), stream)
+        torch.cuda.synchronize()
+        yv = torch.view_as_complex(yh.float().contiguous())
+        err_fwd = float(torch.linalg.vector_norm(yv - y) / torch.linalg.vector_norm(y))
+        i16.execute(yh.data_ptr(), yh.data_ptr(), stream)
+        torch.cuda.synchronize()
+        xr = torch.view_as_complex(xh.float().contiguous())
+        yr = torch.view_as_complex(yh.float().contiguous())
+        err_rt = float(torch.linalg.vector_norm(yr - xr) / torch.linalg.vector_norm(xr))
+        us16 = ms16 / args.steps * 1e3 / 2 / world
+        half[name] = {"us_per_transform": round(us16, 2),
+                      "speedup_vs_c32": round(us_per_transform / us16, 3),
+                      "rel_l2_fwd_vs_c32_path": err_fwd, "rel_l2_roundtrip": err_rt}
+        for p in (f16, i16, f32o):
+            p.close()
+        del xh, yh
+
+    # --- end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.empty(DIMS, dtype=torch.complex64).pin_memory()
+        hx.copy_(x.cpu())
+        hy = torch.empty_like(hx).pin_memory()
+        for _ in range(2):
+            fwd.execute_host(hx.data_ptr(), hy.data_ptr(), stream)
+            inv.execute_host(hy.data_ptr(), hy.data_ptr(), stream)
+        esteps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(esteps):
+            fwd.execute_host(hx.data_ptr(), hy.data_ptr(), stream)
+            inv.execute_host(hy.data_ptr(), hy.data_ptr(), stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        dt = allmax(world, time.perf_counter() - t0)
+        e2e = {"value": round(dt / esteps * 1e6 / 2 / world, 2), "unit": "us",
+               "h2d_bytes_per_step": 2 * ELEMS * 8, "d2h_bytes_per_step": 2 * ELEMS * 8,
+               "steps": esteps, "entry": "wsfft_execute_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_sample_oracle()
+
+    if rank == 0:
+        min_bytes = REF_PASSES * 2 * ELEMS * 8
+        line = {
+            "metric": METRIC, "value": round(us_per_transform, 2), "unit": "us",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_per_step, 4), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dims": list(DIMS), "dtype": "complex64",
+                       "input": "N(0,1) re/im, seeded, device-generated",
+                       "l2": "inputs larger than L2 (1 GiB array vs 126 MB L2)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "gflops": round(FLOPS / (us_per_transform * 1e-6) / 1e9 * 1.0, 1),
+            "hbm_min_bytes_roofline": {
+                "passes": REF_PASSES, "bytes": min_bytes,
+                "time_us_at_peak": round(min_bytes / (hbm_peak * 1e9) * 1e6, 1),
+                "frac": round(min_bytes / (hbm_peak * 1e9) / (us_per_transform * 1e-6), 4),
+                "peak_gbs": hbm_peak, "peak_kind": peak_kind},
+            "passes_used": npass,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                         "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                         "traffic": traffic, "kernel": f"pass {dom} of {npass}",
+                         "per_pass_ms": [round(v, 4) for v in mean_ms],
+                         "bytes_per_launch": bytes_launch, "peak_kind": peak_kind},
+            "rel_l2_roundtrip_c32": rt32,
+            "half_storage": half,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "paper_cs2_us": PAPER_CS2_US,
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    for p in (fwd, inv):
+        p.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

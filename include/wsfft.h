@@ -1,0 +1,179 @@
+/*
+ * wsfft -- multidimensional complex-to-complex FFT for sm_103a GPUs.
+ *
+ * The operation is the k-superstep multidimensional FFT of "Wafer-Scale Fast
+ * Fourier Transforms" (Orenes-Vera et al.): for a rank-k array of complex
+ * numbers, one superstep per axis applies a batch of 1D Cooley-Tukey FFTs
+ * along that axis (Section 1; Section 2.1, pencil decomposition; Section 4.1,
+ * pencil computation).  Between supersteps the paper redistributes the data
+ * over its processor mesh (Section 4.3); here that redistribution is done on
+ * the chip, inside the kernels' strided loads and stores.
+ *
+ * Definition (Section 1, with the sign numpy uses; numpy is the paper's
+ * validator, Section 4.1):
+ *
+ *   forward:  X[k] = sum_j x[j] exp(-2 pi i sum_d j_d k_d / n_d)
+ *   inverse:  x[j] = s * sum_k X[k] exp(+2 pi i sum_d j_d k_d / n_d)
+ *
+ * where s depends on the normalisation (wsfft_plan_set_norm).
+ *
+ * Conventions shared by every entry point:
+ *  - Layout: row-major; dims[rank-1] is the contiguous axis (Section 1:
+ *    element (i,j,k) is element k of pencil (i,j)).  A batch of independent
+ *    transforms is the outermost dimension, with stride prod(dims).
+ *  - Complex numbers are interleaved (re, im): WSFFT_C32 = two float32 (8 B),
+ *    WSFFT_C16F = two IEEE float16 (4 B), WSFFT_C16BF = two bfloat16 (4 B).
+ *    Reduced-precision storage is computed in float32 with float32 twiddles
+ *    and rounded to the storage type (round-to-nearest-even) at the end of
+ *    each pass (Section 4.1 offers FP16 and FP32 storage).
+ *  - Sizes: every axis a power of two (Section 4.4: power-of-two sizes only);
+ *    axes up to 4096 for rank 2 and 3, up to 2^24 for rank 1.  Other sizes
+ *    return WSFFT_ERR_INVALID_SIZE.
+ *  - Pointers passed to execute are device pointers (unless named host_*),
+ *    owned by the caller, 16-byte aligned, and must stay valid until the
+ *    enqueued work completes.  in == out (in place) is allowed; otherwise in
+ *    and out must not overlap.  `in` is never written when in != out.
+ *  - Streams are cudaStream_t values passed as wsfft_stream (NULL = the legacy
+ *    default stream).  Execute calls are asynchronous on that stream.
+ *  - Every function returns a wsfft_status.  No other error state is kept,
+ *    except the per-plan device status word, which a device-side timeout
+ *    sets; it is reported by wsfft_plan_sync_status.
+ *  - A plan belongs to the CUDA device that was current when it was created
+ *    and must be used with that device current.  Plans are not thread-safe:
+ *    do not call execute on one plan from two host threads at once.
+ */
+#ifndef WSFFT_H_
+#define WSFFT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wsfft_plan_s *wsfft_plan;   /* opaque, owned by the library */
+typedef struct CUstream_st *wsfft_stream;  /* same type as cudaStream_t */
+
+typedef enum {
+    WSFFT_C32 = 0,   /* complex64: float32 re, float32 im */
+    WSFFT_C16F = 1,  /* float16 re, float16 im */
+    WSFFT_C16BF = 2  /* bfloat16 re, bfloat16 im */
+} wsfft_dtype;
+
+typedef enum {
+    WSFFT_FORWARD = -1, /* exponent sign -1 */
+    WSFFT_INVERSE = 1   /* exponent sign +1 (conjugated roots, Section 4.2) */
+} wsfft_direction;
+
+typedef enum {
+    /* Section 4.2: the inverse multiplies the result of each compute stage by
+     * 1/n of that stage's axis, 1/N in total; the forward is unscaled. */
+    WSFFT_NORM_PAPER = 0,
+    /* never scaled: the inverse is then the adjoint of the forward */
+    WSFFT_NORM_NONE = 1,
+    /* each superstep scaled by 1/sqrt(n_d), both directions (unitary); the
+     * default for reduced-precision storage, which keeps values in range */
+    WSFFT_NORM_ORTHO = 2,
+    /* the forward scaled by 1/n_d per superstep, the inverse unscaled: the
+     * adjoint of an inverse under WSFFT_NORM_PAPER */
+    WSFFT_NORM_FORWARD = 3
+} wsfft_norm;
+
+typedef enum {
+    WSFFT_SUCCESS = 0,
+    WSFFT_ERR_INVALID_ARG = -1,   /* null/misaligned pointer, bad enum, bad rank */
+    WSFFT_ERR_INVALID_SIZE = -2,  /* non-power-of-two or out-of-range axis */
+    WSFFT_ERR_UNSUPPORTED = -3,   /* valid request this build does not handle */
+    WSFFT_ERR_ALLOC = -4,         /* device or host allocation failed */
+    WSFFT_ERR_CUDA = -5,          /* a CUDA runtime call failed */
+    WSFFT_ERR_DEVICE_TIMEOUT = -6 /* a bounded device-side wait ran out */
+} wsfft_status;
+
+/* Create a plan for `batch` independent rank-`rank` transforms of shape
+ * dims[0..rank-1] (row-major, dims[rank-1] contiguous).
+ *   plan      out: the new plan (NULL on failure)
+ *   dims      host array of `rank` axis lengths, each a power of two
+ *   rank      1, 2 or 3
+ *   dtype     a wsfft_dtype; direction a wsfft_direction
+ *   batch     >= 1
+ * Builds the pass schedule and the twiddle tables (computed in FP64 on the
+ * host, rounded to FP32, uploaded once) on the current device.  Default
+ * normalisation: WSFFT_NORM_PAPER for WSFFT_C32, WSFFT_NORM_ORTHO otherwise.
+ * Errors: INVALID_ARG, INVALID_SIZE, ALLOC, CUDA.  Sections 1, 4.1, 4.2. */
+int wsfft_plan_create(wsfft_plan *plan, const int64_t *dims, int rank, int dtype,
+                      int direction, int64_t batch);
+
+/* Change the normalisation (a wsfft_norm).  Section 4.2.
+ * Errors: INVALID_ARG. */
+int wsfft_plan_set_norm(wsfft_plan plan, int norm);
+
+/* Enqueue the transform of `batch` arrays from `in` to `out` on `stream`.
+ * in/out: device pointers to batch*prod(dims) elements of the plan's dtype.
+ * Section 1 (supersteps), Section 4.2 (3D sequence), Section 4.3
+ * (redistribution, here fused into the kernels' loads and stores).
+ * Errors: INVALID_ARG (null or misaligned pointer), CUDA (launch failure),
+ * DEVICE_TIMEOUT (an earlier execute on this plan timed out on the device;
+ * the status is cleared when returned). */
+int wsfft_execute(wsfft_plan plan, const void *in, void *out, wsfft_stream stream);
+
+/* Same transform with HOST buffers: copies host_in to a plan-owned device
+ * buffer, transforms, copies back to host_out, and waits for the stream.
+ * host_in/host_out should be page-locked for full copy speed.  The first
+ * call allocates the device buffer (2 * batch * prod(dims) elements).
+ * Errors: as wsfft_execute, plus ALLOC. */
+int wsfft_execute_host(wsfft_plan plan, const void *host_in, void *host_out,
+                       wsfft_stream stream);
+
+/* Release the plan and every device allocation it owns.  Synchronises the
+ * plan's device first.  NULL is accepted.  Errors: CUDA. */
+int wsfft_destroy(wsfft_plan plan);
+
+/* Plan for `count` independent rank-3 transforms of uneven shapes
+ * dims[3*i .. 3*i+2] (each axis a power of two, 2..4096), executed by one
+ * persistent launch that pulls (instance, pass, tile) tasks from a queue.
+ * Section 4.4 (more than one pencil per processor) generalised to one
+ * processor per tile.  Errors: INVALID_ARG, INVALID_SIZE, ALLOC, CUDA. */
+int wsfft_plan_create_ragged(wsfft_plan *plan, int count, const int64_t *dims,
+                             int dtype, int direction);
+
+/* Enqueue a ragged plan: in[i], out[i] are device pointers for instance i
+ * (host arrays of `count` pointers).  Errors: as wsfft_execute. */
+int wsfft_execute_ragged(wsfft_plan plan, const void *const *in, void *const *out,
+                         wsfft_stream stream);
+
+/* Time the kernel variants that apply to this plan on `stream` (with
+ * temporary buffers) and keep the fastest; results are cached in the JSON
+ * file named by WSFFT_TUNE_CACHE (if set), keyed by device name, SM count,
+ * shape, dtype and direction.  Errors: ALLOC, CUDA. */
+int wsfft_autotune(wsfft_plan plan, wsfft_stream stream);
+
+/* Synchronise `stream`, then return and clear the plan's device status word
+ * (WSFFT_SUCCESS or WSFFT_ERR_DEVICE_TIMEOUT).  Errors: CUDA. */
+int wsfft_plan_sync_status(wsfft_plan plan, wsfft_stream stream);
+
+/* Number of passes over the array one execute makes, and the minimum number
+ * of bytes one execute reads plus writes in HBM for that schedule. */
+int wsfft_plan_passes(wsfft_plan plan, int *passes, int64_t *bytes_per_execute);
+
+/* Per-launch timing (the paper times compute and communication phases
+ * separately, Section 5.2).  capacity > 0 makes every later kernel launch of
+ * this plan record a pair of CUDA events on the execute stream, for up to
+ * `capacity` launches; 0 turns recording off and frees the events.
+ * Errors: INVALID_ARG, ALLOC, CUDA. */
+int wsfft_plan_profile(wsfft_plan plan, int capacity);
+
+/* Wait for the recorded launches, write the elapsed milliseconds of each
+ * (in launch order, at most `capacity` values) to ms[], the number of
+ * launches recorded to *count, and start a new recording.  ms may be NULL
+ * to only reset.  Errors: INVALID_ARG, CUDA. */
+int wsfft_plan_launch_times(wsfft_plan plan, float *ms, int capacity, int *count);
+
+/* Static text for a status code. */
+const char *wsfft_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WSFFT_H_ */

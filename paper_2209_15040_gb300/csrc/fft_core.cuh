@@ -1,0 +1,238 @@
+// Register-resident pencil FFT core for sm_103a.
+//
+// One pencil of length N is spread over T = N/E threads, each holding E
+// complex values in registers.  The transform is the self-sorting (Stockham)
+// form of Cooley-Tukey: stage s combines R_s-point DFTs, multiplies by the
+// roots of unity of that level, and writes its results in an order that
+// leaves the final output in natural order.  This is the role the paper's
+// even/odd "reshape" plays after each radix-2 level (Section 4.1), done here
+// with radix-8/16 butterflies in registers and one shared-memory exchange
+// between stages instead of a reshape per level.
+//
+// Stage s (radix R, Ns = product of the earlier radices), butterfly b in
+// [0, N/R):   a[r] = X[b + r*N/R] * w_{Ns*R}^{r*(b mod Ns)},  a = DFT_R(a),
+//             Y[(b div Ns)*Ns*R + (b mod Ns) + r*Ns] = a[r]
+// with w_m = exp(-2*pi*i/m) (forward sign, Section 1).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wsfft {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// a * exp(-2*pi*i*J/16) for a compile-time J.  The constants are cos and sin
+// of multiples of pi/8.
+template <int J>
+__device__ __forceinline__ float2 rot16(float2 a) {
+    constexpr int j = ((J % 16) + 16) % 16;
+    constexpr float H = 0.70710678118654752440f;   // cos(pi/4)
+    constexpr float C1 = 0.92387953251128675613f;  // cos(pi/8)
+    constexpr float S1 = 0.38268343236508977173f;  // sin(pi/8)
+    if constexpr (j == 0) {
+        return a;
+    } else if constexpr (j == 4) {
+        return make_float2(a.y, -a.x);
+    } else if constexpr (j == 8) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (j == 12) {
+        return make_float2(-a.y, a.x);
+    } else if constexpr (j == 2) {
+        return make_float2((a.x + a.y) * H, (a.y - a.x) * H);
+    } else if constexpr (j == 6) {
+        return make_float2((a.y - a.x) * H, -(a.x + a.y) * H);
+    } else if constexpr (j == 10) {
+        return make_float2(-(a.x + a.y) * H, (a.x - a.y) * H);
+    } else if constexpr (j == 14) {
+        return make_float2((a.x - a.y) * H, (a.x + a.y) * H);
+    } else {
+        // odd j: cos and sin of 2*pi*j/16 are +-cos(pi/8) or +-sin(pi/8)
+        constexpr float c = (j == 1) ? C1 : (j == 3) ? S1 : (j == 5) ? -S1 : (j == 7) ? -C1
+                          : (j == 9) ? -C1 : (j == 11) ? -S1 : (j == 13) ? S1 : C1;
+        constexpr float s = (j == 1) ? S1 : (j == 3) ? C1 : (j == 5) ? C1 : (j == 7) ? S1
+                          : (j == 9) ? -S1 : (j == 11) ? -C1 : (j == 13) ? -C1 : -S1;
+        // (x + iy)(c - is) = (xc + ys) + i(yc - xs)
+        return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+    }
+}
+
+// In-register R-point forward DFT (R in {1,2,4,8,16}), natural order in and
+// out: split into even and odd halves, transform each, combine with
+// exp(-2*pi*i*k/R).
+template <int R, int K>
+__device__ __forceinline__ void dft_combine(float2 (&a)[R], const float2 (&e)[R / 2],
+                                            const float2 (&o)[R / 2]) {
+    if constexpr (K < R / 2) {
+        const float2 t = rot16<K * (16 / R)>(o[K]);
+        a[K] = cadd(e[K], t);
+        a[K + R / 2] = csub(e[K], t);
+        dft_combine<R, K + 1>(a, e, o);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void dft(float2 (&a)[R]) {
+    static_assert(R == 1 || R == 2 || R == 4 || R == 8 || R == 16, "radix");
+    if constexpr (R == 2) {
+        const float2 t = a[0];
+        a[0] = cadd(t, a[1]);
+        a[1] = csub(t, a[1]);
+    } else if constexpr (R > 2) {
+        float2 e[R / 2], o[R / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+            e[i] = a[2 * i];
+            o[i] = a[2 * i + 1];
+        }
+        dft<R / 2>(e);
+        dft<R / 2>(o);
+        dft_combine<R, 0>(a, e, o);
+    }
+}
+
+// Stage schedule for a pencil of length N with E values per thread: every
+// stage has radix E except the last, whose radix is whatever remains.  The
+// host plan builder calls the same functions to lay out the twiddle tables.
+__host__ __device__ constexpr int sched_nstages(int N, int E) {
+    int s = 0;
+    long ns = 1;
+    while (ns < N) {
+        ns *= E;
+        ++s;
+    }
+    return s < 1 ? 1 : s;
+}
+__host__ __device__ constexpr int sched_ns_before(int N, int E, int s) {
+    long ns = 1;
+    for (int i = 0; i < s; ++i) ns *= E;
+    return ns > N ? N : (int)ns;
+}
+__host__ __device__ constexpr int sched_radix(int N, int E, int s) {
+    return (N / sched_ns_before(N, E, s) < E) ? N / sched_ns_before(N, E, s) : E;
+}
+// stage s >= 1 reads twiddles tw[off(s) + (r-1)*Ns + k] = w_{Ns*R}^{r*k},
+// r in [1,R), k in [0,Ns)
+__host__ __device__ constexpr int sched_tw_offset(int N, int E, int s) {
+    int off = 0;
+    for (int i = 1; i < s; ++i) off += (sched_radix(N, E, i) - 1) * sched_ns_before(N, E, i);
+    return off;
+}
+__host__ __device__ constexpr int sched_tw_size(int N, int E) {
+    return sched_tw_offset(N, E, sched_nstages(N, E));
+}
+
+template <int N, int E>
+struct Sched {
+    static_assert(E >= 1 && E <= 16 && (E & (E - 1)) == 0, "E");
+    static_assert(N >= E && (N & (N - 1)) == 0, "N");
+    static constexpr int T = N / E;  // threads per pencil
+    __host__ __device__ static constexpr int nstages() { return sched_nstages(N, E); }
+    __host__ __device__ static constexpr int ns_before(int s) { return sched_ns_before(N, E, s); }
+    __host__ __device__ static constexpr int radix(int s) { return sched_radix(N, E, s); }
+    __host__ __device__ static constexpr int tw_offset(int s) { return sched_tw_offset(N, E, s); }
+    __host__ __device__ static constexpr int tw_size() { return sched_tw_size(N, E); }
+};
+
+// Runs stages S_IDX.. of the pencil transform.  `a` holds the outputs of
+// stage S_IDX-1 for this thread's butterflies.  Acc provides
+//   gload(k), gstore(k, v)  -- global element k of this thread's pencil
+//   sstore(k, v), sload(k)  -- shared-memory element k of the pencil
+//   sync()                  -- barrier over every thread that shares the tile
+template <int N, int E, int S_IDX, class Acc>
+__device__ __forceinline__ void run_stages(float2 (&a)[E], Acc &acc, int t,
+                                           const float2 *__restrict__ tw) {
+    using S = Sched<N, E>;
+    constexpr int T = S::T;
+    constexpr int NsPrev = S::ns_before(S_IDX - 1);
+    constexpr int Rprev = S::radix(S_IDX - 1);
+    constexpr int Mprev = E / Rprev;
+    if constexpr (S_IDX == S::nstages()) {
+        // previous stage was the last: Ns*R == N, so its output index is b + r*Ns
+#pragma unroll
+        for (int i = 0; i < Mprev; ++i)
+#pragma unroll
+            for (int r = 0; r < Rprev; ++r) acc.gstore(t + T * i + r * NsPrev, a[i * Rprev + r]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Mprev; ++i) {
+            const int b = t + T * i;
+            const int base = (b / NsPrev) * NsPrev * Rprev + (b % NsPrev);
+#pragma unroll
+            for (int r = 0; r < Rprev; ++r) acc.sstore(base + r * NsPrev, a[i * Rprev + r]);
+        }
+        acc.sync();
+        constexpr int Ns = NsPrev * Rprev;
+        constexpr int R = S::radix(S_IDX);
+        constexpr int M = E / R;
+        constexpr int TWO = S::tw_offset(S_IDX);
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[i * R + r] = acc.sload(t + T * i + r * (N / R));
+        acc.sync();
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int k = (t + T * i) % Ns;
+            float2 g[R];
+            g[0] = a[i * R];
+#pragma unroll
+            for (int r = 1; r < R; ++r) g[r] = cmul(a[i * R + r], __ldg(&tw[TWO + (r - 1) * Ns + k]));
+            dft<R>(g);
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[i * R + r] = g[r];
+        }
+        run_stages<N, E, S_IDX + 1>(a, acc, t, tw);
+    }
+}
+
+// Whole pencil: first stage straight from global memory, last stage straight
+// to global memory, shared-memory exchanges in between.
+template <int N, int E, class Acc>
+__device__ __forceinline__ void pencil_fft(Acc &acc, int t, const float2 *__restrict__ tw) {
+    constexpr int T = Sched<N, E>::T;
+    float2 a[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) a[r] = acc.gload(t + r * T);
+    dft<E>(a);
+    run_stages<N, E, 1>(a, acc, t, tw);
+}
+
+// ---------------------------------------------------------------------------
+// Storage conversion.  Reduced-precision values are widened to float32 on
+// load and rounded to nearest-even on store.
+
+template <class S>
+struct Cvt;
+
+template <>
+struct Cvt<float2> {
+    __device__ __forceinline__ static float2 load(const float2 *p) { return *p; }
+    __device__ __forceinline__ static void store(float2 *p, float2 v) { *p = v; }
+};
+
+template <>
+struct Cvt<__half2> {
+    __device__ __forceinline__ static float2 load(const __half2 *p) { return __half22float2(*p); }
+    __device__ __forceinline__ static void store(__half2 *p, float2 v) { *p = __float22half2_rn(v); }
+};
+
+template <>
+struct Cvt<__nv_bfloat162> {
+    __device__ __forceinline__ static float2 load(const __nv_bfloat162 *p) {
+        return __bfloat1622float2(*p);
+    }
+    __device__ __forceinline__ static void store(__nv_bfloat162 *p, float2 v) {
+        *p = __float22bfloat162_rn(v);
+    }
+};
+
+}  // namespace wsfft

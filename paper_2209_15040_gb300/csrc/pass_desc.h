@@ -1,0 +1,34 @@
+// Per-launch arguments of a superstep kernel and the launcher entry points
+// that the host plan code calls (one set per storage type).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wsfft {
+
+struct PassArgs {
+    int64_t npencils;   // outer * inner pencils in this launch
+    int64_t inner;      // element stride between consecutive pencil elements
+    int log_inner;      // log2(inner)
+    const float2 *tw;   // stage twiddle table of this (N, E) schedule
+    float conj_in;      // +1, or -1 to conjugate every loaded value
+    float sx, sy;       // store scale of re and im (sy = -sx conjugates)
+    int64_t trans_rows; // contiguous transposed store: rows per transform
+    float tw_inv;       // four-step twiddle: 2 / L
+    int tw_mask;        // four-step twiddle: L - 1
+};
+
+enum PassKind { PASS_CONTIG = 0, PASS_STRIDED = 1 };
+
+// Launch one superstep.  variant: contiguous -> transposed store,
+// strided -> four-step twiddle on store.  Returns cudaErrorInvalidValue for
+// a (kind, N, E) combination this build does not instantiate.
+cudaError_t launch_pass_c32(int kind, int N, int E, bool variant, const void *in, void *out,
+                            const PassArgs &a, cudaStream_t st);
+cudaError_t launch_pass_c16f(int kind, int N, int E, bool variant, const void *in, void *out,
+                             const PassArgs &a, cudaStream_t st);
+cudaError_t launch_pass_c16bf(int kind, int N, int E, bool variant, const void *in, void *out,
+                              const PassArgs &a, cudaStream_t st);
+
+}  // namespace wsfft

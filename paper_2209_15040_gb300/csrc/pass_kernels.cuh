@@ -1,0 +1,196 @@
+// Superstep kernels: one launch transforms every pencil along one axis.
+//
+// The array is viewed, for the axis being transformed, as [outer][N][inner]
+// elements: `inner` is the product of the later axes (1 for the contiguous
+// axis), `outer` the product of the earlier axes and the batch.  A pencil is
+// one (outer, inner) pair (Section 2.1, pencil decomposition); the paper's
+// processing element that owns a pencil becomes a group of T = N/E threads,
+// and the redistribution between supersteps (Section 4.3) becomes the choice
+// of which pencils a thread block gathers:
+//
+//  * contiguous axis (inner == 1): a block takes P whole pencils, each a
+//    contiguous run of N elements; threads of a pencil are consecutive, so
+//    each warp-wide load or store touches consecutive addresses.
+//  * strided axis (inner > 1): a block takes W pencils that are adjacent in
+//    memory (consecutive inner index).  Row k of the tile is W consecutive
+//    elements, so the "transpose" of the paper is fused into loads and stores
+//    that read whole 128-byte rows; the pencil index is the fastest thread
+//    index, which keeps shared-memory exchanges free of bank conflicts.
+#pragma once
+
+#include "fft_core.cuh"
+#include "pass_desc.h"
+
+namespace wsfft {
+
+// Elements per thread for an axis of length N (the default variant).
+__host__ __device__ constexpr int default_E(int N) {
+    return N <= 16 ? N : (N <= 64 ? 8 : (N == 512 ? 8 : 16));
+}
+// pencils per block, contiguous axis
+__host__ __device__ constexpr int contig_P(int N, int E, bool trans) {
+    return trans ? ((N / E) >= 64 ? 1024 / (N / E) : (256 / (N / E) > 16 ? 256 / (N / E) : 16))
+                 : ((N / E) >= 256 ? 1 : 256 / (N / E));
+}
+// pencils per block, strided axis
+__host__ __device__ constexpr int strided_W(int N, int E) {
+    return (N / E) >= 16 ? ((N / E) <= 64 ? 16 : 1024 / (N / E)) : 256 / (N / E);
+}
+// shared-memory row stride (complex elements) of one pencil, contiguous axis
+__host__ __device__ constexpr int contig_PS(int N) { return N + N / 16 + 4; }
+
+__host__ __device__ constexpr int contig_smem_elems(int N, int E, bool trans) {
+    return (N / E) == 1 && !trans
+               ? 0
+               : (contig_P(N, E, trans) * contig_PS(N) >
+                          (trans ? N * (contig_P(N, E, trans) + 1) : 0)
+                      ? contig_P(N, E, trans) * contig_PS(N)
+                      : N * (contig_P(N, E, trans) + 1));
+}
+__host__ __device__ constexpr int strided_smem_elems(int N, int E) {
+    return (N / E) == 1 ? 0 : N * strided_W(N, E) + (N * strided_W(N, E)) / 16;
+}
+
+// Epilogue: optional four-step twiddle, then scale and conjugate.
+struct Epi {
+    float sx, sy;  // multiply re by sx, im by sy (sy = -sx conjugates)
+};
+
+template <class S>
+struct ContigAcc {
+    const S *in;   // this pencil's first element
+    S *out;        // this pencil's first element (unused when transposing)
+    float2 *sm;    // this pencil's shared-memory row
+    float ci;      // +1, or -1 to conjugate on load
+    Epi epi;
+    bool active;
+    __device__ __forceinline__ float2 gload(int k) const {
+        float2 v = active ? Cvt<S>::load(in + k) : make_float2(0.f, 0.f);
+        v.y *= ci;
+        return v;
+    }
+    __device__ __forceinline__ void gstore(int k, float2 v) const {
+        if (active) Cvt<S>::store(out + k, make_float2(v.x * epi.sx, v.y * epi.sy));
+    }
+    __device__ __forceinline__ void sstore(int k, float2 v) const { sm[k + (k >> 4)] = v; }
+    __device__ __forceinline__ float2 sload(int k) const { return sm[k + (k >> 4)]; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+// Contiguous axis, transposed store for the four-step split of a long 1D
+// axis: the result of pencil p (row k2 of transform b) element k goes to
+// out[b*N + k*rows + k2], staged through shared memory so the global store
+// is P consecutive elements per k.
+template <class S>
+struct ContigTransAcc : ContigAcc<S> {
+    float2 *stage;  // [N][P+1] staging
+    int p, P;
+    __device__ __forceinline__ void gstore(int k, float2 v) const { stage[k * (P + 1) + p] = v; }
+};
+
+template <int N, int E, int P, class S, bool TRANS>
+__global__ void __launch_bounds__(P *(N / E))
+    contig_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
+    extern __shared__ float2 smem[];
+    constexpr int T = N / E;
+    const int t = threadIdx.x % T;
+    const int p = threadIdx.x / T;
+    const int64_t tile = blockIdx.x;
+    const int64_t q = tile * P + p;
+    const bool active = q < a.npencils;
+    if constexpr (!TRANS) {
+        ContigAcc<S> acc{in + q * N, out + q * N, smem + p * contig_PS(N), a.conj_in, {a.sx, a.sy},
+                         active};
+        pencil_fft<N, E>(acc, t, a.tw);
+    } else {
+        ContigTransAcc<S> acc;
+        acc.in = in + q * N;
+        acc.out = nullptr;
+        acc.sm = smem + p * contig_PS(N);
+        acc.ci = a.conj_in;
+        acc.epi = {a.sx, a.sy};
+        acc.active = active;
+        acc.stage = smem;
+        acc.p = p;
+        acc.P = P;
+        pencil_fft<N, E>(acc, t, a.tw);
+        __syncthreads();
+        // rows per transform a.trans_rows is a multiple of P, so the tile's
+        // rows belong to one transform
+        const int64_t q0 = tile * P;
+        const int64_t b = q0 / a.trans_rows;
+        const int64_t row0 = q0 - b * a.trans_rows;
+        S *ob = out + b * (int64_t)N * a.trans_rows + row0;
+        for (int idx = threadIdx.x; idx < N * P; idx += P * T) {
+            const int pp = idx % P, k = idx / P;
+            if (q0 + pp < a.npencils) {
+                const float2 v = smem[k * (P + 1) + pp];
+                Cvt<S>::store(ob + (int64_t)k * a.trans_rows + pp,
+                              make_float2(v.x * a.sx, v.y * a.sy));
+            }
+        }
+    }
+}
+
+template <class S, bool TWID>
+struct StridedAcc {
+    const S *in;   // this pencil's first element
+    S *out;
+    float2 *sm;    // tile base in shared memory
+    int64_t stride;
+    int w, W;
+    float ci;
+    Epi epi;
+    bool active;
+    int twq;        // four-step: inner index of this pencil
+    float tw_inv;   // four-step: 2 / (length of the long transform)
+    int tw_mask;    // four-step: length - 1
+    __device__ __forceinline__ float2 gload(int k) const {
+        float2 v = active ? Cvt<S>::load(in + (int64_t)k * stride) : make_float2(0.f, 0.f);
+        v.y *= ci;
+        return v;
+    }
+    __device__ __forceinline__ void gstore(int k, float2 v) const {
+        if constexpr (TWID) {
+            // w_L^(q*k), L = tw_mask + 1; the angle 2*m/L is exact in float
+            const int m = (twq * k) & tw_mask;
+            float s, c;
+            sincospif((float)m * tw_inv, &s, &c);
+            v = cmul(v, make_float2(c, -s));
+        }
+        if (active) Cvt<S>::store(out + (int64_t)k * stride, make_float2(v.x * epi.sx, v.y * epi.sy));
+    }
+    __device__ __forceinline__ int sidx(int k) const { return k * W + w + ((k * W) >> 4); }
+    __device__ __forceinline__ void sstore(int k, float2 v) const { sm[sidx(k)] = v; }
+    __device__ __forceinline__ float2 sload(int k) const { return sm[sidx(k)]; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+template <int N, int E, int W, class S, bool TWID>
+__global__ void __launch_bounds__(W *(N / E))
+    strided_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
+    extern __shared__ float2 smem[];
+    const int w = threadIdx.x % W;
+    const int t = threadIdx.x / W;
+    const int64_t q = (int64_t)blockIdx.x * W + w;
+    const bool active = q < a.npencils;
+    const int64_t o = q >> a.log_inner;
+    const int64_t i = q & (a.inner - 1);
+    const int64_t base = o * ((int64_t)N << a.log_inner) + i;
+    StridedAcc<S, TWID> acc;
+    acc.in = in + base;
+    acc.out = out + base;
+    acc.sm = smem;
+    acc.stride = a.inner;
+    acc.w = w;
+    acc.W = W;
+    acc.ci = a.conj_in;
+    acc.epi = {a.sx, a.sy};
+    acc.active = active;
+    acc.twq = (int)i;
+    acc.tw_inv = a.tw_inv;
+    acc.tw_mask = a.tw_mask;
+    pencil_fft<N, E>(acc, t, a.tw);
+}
+
+}  // namespace wsfft

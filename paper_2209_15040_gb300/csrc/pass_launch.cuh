@@ -1,0 +1,91 @@
+// Instantiation and dispatch of the superstep kernels for one storage type.
+// Included once per storage type by pass_c32.cu, pass_c16f.cu, pass_c16bf.cu
+// (with WSFFT_STORE and WSFFT_LAUNCH_NAME defined) so the three compile in
+// parallel.
+#pragma once
+
+#include "pass_kernels.cuh"
+
+namespace wsfft {
+namespace {
+
+template <class K>
+cudaError_t set_smem(K kernel, int bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int N, int E, class S, bool TRANS>
+cudaError_t launch_contig(const void *in, void *out, const PassArgs &a, cudaStream_t st) {
+    constexpr int T = N / E;
+    constexpr int P = contig_P(N, E, TRANS);
+    constexpr int smem = contig_smem_elems(N, E, TRANS) * (int)sizeof(float2);
+    auto kern = contig_kernel<N, E, P, S, TRANS>;
+    static cudaError_t attr = set_smem(kern, smem);
+    if (attr != cudaSuccess) return attr;
+    const int64_t blocks = (a.npencils + P - 1) / P;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    kern<<<(unsigned)blocks, P * T, smem, st>>>((const S *)in, (S *)out, a);
+    return cudaGetLastError();
+}
+
+template <int N, int E, class S, bool TWID>
+cudaError_t launch_strided(const void *in, void *out, const PassArgs &a, cudaStream_t st) {
+    constexpr int T = N / E;
+    constexpr int W = strided_W(N, E);
+    constexpr int smem = strided_smem_elems(N, E) * (int)sizeof(float2);
+    auto kern = strided_kernel<N, E, W, S, TWID>;
+    static cudaError_t attr = set_smem(kern, smem);
+    if (attr != cudaSuccess) return attr;
+    const int64_t blocks = (a.npencils + W - 1) / W;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    kern<<<(unsigned)blocks, W * T, smem, st>>>((const S *)in, (S *)out, a);
+    return cudaGetLastError();
+}
+
+template <int N, int E, class S>
+cudaError_t launch_n(int kind, bool variant, const void *in, void *out, const PassArgs &a,
+                     cudaStream_t st) {
+    if (kind == PASS_CONTIG) {
+        if (!variant) return launch_contig<N, E, S, false>(in, out, a, st);
+        if constexpr (N >= 64) return launch_contig<N, E, S, true>(in, out, a, st);
+    } else {
+        if (!variant) return launch_strided<N, E, S, false>(in, out, a, st);
+        if constexpr (N >= 64) return launch_strided<N, E, S, true>(in, out, a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t WSFFT_LAUNCH_NAME(int kind, int N, int E, bool variant, const void *in, void *out,
+                              const PassArgs &a, cudaStream_t st) {
+    using S = WSFFT_STORE;
+#define WSFFT_CASE(n)                                                              \
+    case n:                                                                        \
+        if (E == default_E(n)) return launch_n<n, default_E(n), S>(kind, variant, in, out, a, st); \
+        break;
+    switch (N) {
+        WSFFT_CASE(1)
+        WSFFT_CASE(2)
+        WSFFT_CASE(4)
+        WSFFT_CASE(8)
+        WSFFT_CASE(16)
+        WSFFT_CASE(32)
+        WSFFT_CASE(64)
+        WSFFT_CASE(128)
+        WSFFT_CASE(256)
+        WSFFT_CASE(512)
+        WSFFT_CASE(1024)
+        WSFFT_CASE(2048)
+        WSFFT_CASE(4096)
+        default:
+            break;
+    }
+#undef WSFFT_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace wsfft
