@@ -112,9 +112,9 @@ int wsfft_plan_set_norm(wsfft_plan plan, int norm);
  * in/out: device pointers to batch*prod(dims) elements of the plan's dtype.
  * Section 1 (supersteps), Section 4.2 (3D sequence), Section 4.3
  * (redistribution, here fused into the kernels' loads and stores).
- * Errors: INVALID_ARG (null or misaligned pointer), CUDA (launch failure),
- * DEVICE_TIMEOUT (an earlier execute on this plan timed out on the device;
- * the status is cleared when returned). */
+ * Errors: INVALID_ARG (null or misaligned pointer), CUDA (launch failure).
+ * A device-side timeout is not reported here (the call does not wait for
+ * the device); wsfft_plan_sync_status reports it. */
 int wsfft_execute(wsfft_plan plan, const void *in, void *out, wsfft_stream stream);
 
 /* Same transform with HOST buffers: copies host_in to a plan-owned device
@@ -147,6 +147,37 @@ int wsfft_execute_ragged(wsfft_plan plan, const void *const *in, void *const *ou
  * file named by WSFFT_TUNE_CACHE (if set), keyed by device name, SM count,
  * shape, dtype and direction.  Errors: ALLOC, CUDA. */
 int wsfft_autotune(wsfft_plan plan, wsfft_stream stream);
+
+/* Choose the kernel shape of pass `pass` (0-based, in launch order) of this
+ * plan: `values_per_thread` complex values per thread (the radix of the
+ * register stages, 8 or 16) and `tile` pencils per thread block; 0 and 0
+ * restore the default.  Used by the autotuner.  Errors: INVALID_ARG,
+ * UNSUPPORTED (that shape is not built for this pass). */
+int wsfft_plan_set_pass_variant(wsfft_plan plan, int pass, int values_per_thread, int tile);
+
+/* Choose the schedule of a rank-3 cube (n^3, n in {128, 256, 512, 1024}):
+ *   0 (default): one launch per superstep (three trips through HBM);
+ *   3 (n <= 512): two trips through HBM with warp-per-pencil
+ *      kernels -- a persistent kernel runs the supersteps along the two inner
+ *      axes slab by slab, re-reading each slab from L2, then one launch runs
+ *      the outer axis;
+ *   1: the same two trips with one-tile-per-block style tiles;
+ *   2: the same two trips on the pipelined engine (one producer warp
+ *      streaming tiles into shared memory with bulk asynchronous copies).
+ * wsfft_autotune times the modes and keeps the fastest.  A mode a shape does not support falls back to one launch per superstep.
+ * Other shapes ignore the setting.  The autotuner uses it.
+ * Errors: INVALID_ARG. */
+int wsfft_plan_set_engine(wsfft_plan plan, int mode);
+
+/* Testing aid for the bounded device-side waits of the persistent engine
+ * (used by rank-3 cube plans): withhold != 0 drops the completion signal of
+ * one tile in later executes, so the tiles that wait for it run out their
+ * budget of timeout_ns nanoseconds per wait; the execute then finishes
+ * early, nothing faults or hangs, and wsfft_plan_sync_status reports
+ * WSFFT_ERR_DEVICE_TIMEOUT.  withhold = 0 restores normal operation (the
+ * budget stays timeout_ns; the default is one second).
+ * Errors: INVALID_ARG, UNSUPPORTED (the plan has no waits). */
+int wsfft_plan_set_wait_test(wsfft_plan plan, int withhold, int64_t timeout_ns);
 
 /* Synchronise `stream`, then return and clear the plan's device status word
  * (WSFFT_SUCCESS or WSFFT_ERR_DEVICE_TIMEOUT).  Errors: CUDA. */

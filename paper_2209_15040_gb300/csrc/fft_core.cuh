@@ -147,6 +147,7 @@ struct Sched {
 //   gload(k), gstore(k, v)  -- global element k of this thread's pencil
 //   sstore(k, v), sload(k)  -- shared-memory element k of the pencil
 //   sync()                  -- barrier over every thread that shares the tile
+//   after_load()            -- called once the first stage's inputs are in registers
 template <int N, int E, int S_IDX, class Acc>
 __device__ __forceinline__ void run_stages(float2 (&a)[E], Acc &acc, int t,
                                            const float2 *__restrict__ tw) {
@@ -202,6 +203,7 @@ __device__ __forceinline__ void pencil_fft(Acc &acc, int t, const float2 *__rest
     float2 a[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) a[r] = acc.gload(t + r * T);
+    acc.after_load();
     dft<E>(a);
     run_stages<N, E, 1>(a, acc, t, tw);
 }
@@ -210,28 +212,55 @@ __device__ __forceinline__ void pencil_fft(Acc &acc, int t, const float2 *__rest
 // Storage conversion.  Reduced-precision values are widened to float32 on
 // load and rounded to nearest-even on store.
 
+// Cache operators for global accesses: default, .cg (L2 only: data another
+// block may have written during this launch), .cs (streaming: read or
+// written once, evict first).
+enum : int { OP_DEF = 0, OP_CG = 1, OP_CS = 2 };
+
+template <int OP, class T>
+__device__ __forceinline__ T ld_op(const T *p) {
+    if constexpr (OP == OP_CG) return __ldcg(p);
+    else if constexpr (OP == OP_CS) return __ldcs(p);
+    else return *p;
+}
+template <int OP, class T>
+__device__ __forceinline__ void st_op(T *p, T v) {
+    if constexpr (OP == OP_CS) __stcs(p, v);
+    else *p = v;
+}
+
 template <class S>
 struct Cvt;
 
 template <>
 struct Cvt<float2> {
-    __device__ __forceinline__ static float2 load(const float2 *p) { return *p; }
-    __device__ __forceinline__ static void store(float2 *p, float2 v) { *p = v; }
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static float2 load(const float2 *p) { return ld_op<OP>(p); }
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static void store(float2 *p, float2 v) { st_op<OP>(p, v); }
 };
 
 template <>
 struct Cvt<__half2> {
-    __device__ __forceinline__ static float2 load(const __half2 *p) { return __half22float2(*p); }
-    __device__ __forceinline__ static void store(__half2 *p, float2 v) { *p = __float22half2_rn(v); }
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static float2 load(const __half2 *p) {
+        return __half22float2(ld_op<OP>(p));
+    }
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static void store(__half2 *p, float2 v) {
+        st_op<OP>(p, __float22half2_rn(v));
+    }
 };
 
 template <>
 struct Cvt<__nv_bfloat162> {
+    template <int OP = OP_DEF>
     __device__ __forceinline__ static float2 load(const __nv_bfloat162 *p) {
-        return __bfloat1622float2(*p);
+        return __bfloat1622float2(ld_op<OP>(p));
     }
+    template <int OP = OP_DEF>
     __device__ __forceinline__ static void store(__nv_bfloat162 *p, float2 v) {
-        *p = __float22bfloat162_rn(v);
+        st_op<OP>(p, __float22bfloat162_rn(v));
     }
 };
 

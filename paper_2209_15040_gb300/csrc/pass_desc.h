@@ -19,16 +19,26 @@ struct PassArgs {
     int tw_mask;        // four-step twiddle: L - 1
 };
 
-enum PassKind { PASS_CONTIG = 0, PASS_STRIDED = 1 };
+enum PassKind {
+    PASS_CONTIG = 0,     // one launch, contiguous axis
+    PASS_STRIDED = 1,    // one launch, strided axis
+    PASS_ENGINE_A = 2,   // pipelined engine: z and y of every slab
+    PASS_ENGINE_B = 3,   // pipelined engine: x
+    PASS_PERSIST_A = 4,  // persistent kernel: z and y of every slab
+    PASS_WP_A = 5,       // warp-per-pencil persistent kernel: z and y of every slab
+    PASS_WP_B = 6,       // warp-per-pencil strided superstep: x
+};
 
 // Launch one superstep.  variant: contiguous -> transposed store,
-// strided -> four-step twiddle on store.  Returns cudaErrorInvalidValue for
-// a (kind, N, E) combination this build does not instantiate.
-cudaError_t launch_pass_c32(int kind, int N, int E, bool variant, const void *in, void *out,
-                            const PassArgs &a, cudaStream_t st);
-cudaError_t launch_pass_c16f(int kind, int N, int E, bool variant, const void *in, void *out,
-                             const PassArgs &a, cudaStream_t st);
-cudaError_t launch_pass_c16bf(int kind, int N, int E, bool variant, const void *in, void *out,
-                              const PassArgs &a, cudaStream_t st);
+// strided -> four-step twiddle on store.  tile: 0 = the default tile shape
+// for (N, E); otherwise pencils per block (P or W) of an extra instantiated
+// shape.  Returns cudaErrorInvalidValue for a combination this build does
+// not instantiate.
+cudaError_t launch_pass_c32(int kind, int N, int E, int tile, bool variant, const void *in,
+                            void *out, const PassArgs &a, cudaStream_t st);
+cudaError_t launch_pass_c16f(int kind, int N, int E, int tile, bool variant, const void *in,
+                             void *out, const PassArgs &a, cudaStream_t st);
+cudaError_t launch_pass_c16bf(int kind, int N, int E, int tile, bool variant, const void *in,
+                              void *out, const PassArgs &a, cudaStream_t st);
 
 }  // namespace wsfft

@@ -39,16 +39,13 @@ __host__ __device__ constexpr int strided_W(int N, int E) {
 // shared-memory row stride (complex elements) of one pencil, contiguous axis
 __host__ __device__ constexpr int contig_PS(int N) { return N + N / 16 + 4; }
 
-__host__ __device__ constexpr int contig_smem_elems(int N, int E, bool trans) {
+__host__ __device__ constexpr int contig_smem_elems(int N, int E, int P, bool trans) {
     return (N / E) == 1 && !trans
                ? 0
-               : (contig_P(N, E, trans) * contig_PS(N) >
-                          (trans ? N * (contig_P(N, E, trans) + 1) : 0)
-                      ? contig_P(N, E, trans) * contig_PS(N)
-                      : N * (contig_P(N, E, trans) + 1));
+               : (P * contig_PS(N) > (trans ? N * (P + 1) : 0) ? P * contig_PS(N) : N * (P + 1));
 }
-__host__ __device__ constexpr int strided_smem_elems(int N, int E) {
-    return (N / E) == 1 ? 0 : N * strided_W(N, E) + (N * strided_W(N, E)) / 16;
+__host__ __device__ constexpr int strided_smem_elems(int N, int E, int W) {
+    return (N / E) == 1 ? 0 : N * W + (N * W) / 16;
 }
 
 // Epilogue: optional four-step twiddle, then scale and conjugate.
@@ -56,7 +53,7 @@ struct Epi {
     float sx, sy;  // multiply re by sx, im by sy (sy = -sx conjugates)
 };
 
-template <class S>
+template <class S, int LOP = OP_DEF, int SOP = OP_DEF>
 struct ContigAcc {
     const S *in;   // this pencil's first element
     S *out;        // this pencil's first element (unused when transposing)
@@ -65,16 +62,17 @@ struct ContigAcc {
     Epi epi;
     bool active;
     __device__ __forceinline__ float2 gload(int k) const {
-        float2 v = active ? Cvt<S>::load(in + k) : make_float2(0.f, 0.f);
+        float2 v = active ? Cvt<S>::template load<LOP>(in + k) : make_float2(0.f, 0.f);
         v.y *= ci;
         return v;
     }
     __device__ __forceinline__ void gstore(int k, float2 v) const {
-        if (active) Cvt<S>::store(out + k, make_float2(v.x * epi.sx, v.y * epi.sy));
+        if (active) Cvt<S>::template store<SOP>(out + k, make_float2(v.x * epi.sx, v.y * epi.sy));
     }
     __device__ __forceinline__ void sstore(int k, float2 v) const { sm[k + (k >> 4)] = v; }
     __device__ __forceinline__ float2 sload(int k) const { return sm[k + (k >> 4)]; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ void after_load() const {}
 };
 
 // Contiguous axis, transposed store for the four-step split of a long 1D
@@ -132,7 +130,7 @@ __global__ void __launch_bounds__(P *(N / E))
     }
 }
 
-template <class S, bool TWID>
+template <class S, bool TWID, int LOP = OP_DEF, int SOP = OP_DEF>
 struct StridedAcc {
     const S *in;   // this pencil's first element
     S *out;
@@ -146,7 +144,7 @@ struct StridedAcc {
     float tw_inv;   // four-step: 2 / (length of the long transform)
     int tw_mask;    // four-step: length - 1
     __device__ __forceinline__ float2 gload(int k) const {
-        float2 v = active ? Cvt<S>::load(in + (int64_t)k * stride) : make_float2(0.f, 0.f);
+        float2 v = active ? Cvt<S>::template load<LOP>(in + (int64_t)k * stride) : make_float2(0.f, 0.f);
         v.y *= ci;
         return v;
     }
@@ -158,12 +156,14 @@ struct StridedAcc {
             sincospif((float)m * tw_inv, &s, &c);
             v = cmul(v, make_float2(c, -s));
         }
-        if (active) Cvt<S>::store(out + (int64_t)k * stride, make_float2(v.x * epi.sx, v.y * epi.sy));
+        if (active)
+            Cvt<S>::template store<SOP>(out + (int64_t)k * stride, make_float2(v.x * epi.sx, v.y * epi.sy));
     }
     __device__ __forceinline__ int sidx(int k) const { return k * W + w + ((k * W) >> 4); }
     __device__ __forceinline__ void sstore(int k, float2 v) const { sm[sidx(k)] = v; }
     __device__ __forceinline__ float2 sload(int k) const { return sm[sidx(k)]; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ void after_load() const {}
 };
 
 template <int N, int E, int W, class S, bool TWID>

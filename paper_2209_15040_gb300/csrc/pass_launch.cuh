@@ -15,11 +15,10 @@ cudaError_t set_smem(K kernel, int bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <int N, int E, class S, bool TRANS>
+template <int N, int E, int P, class S, bool TRANS>
 cudaError_t launch_contig(const void *in, void *out, const PassArgs &a, cudaStream_t st) {
     constexpr int T = N / E;
-    constexpr int P = contig_P(N, E, TRANS);
-    constexpr int smem = contig_smem_elems(N, E, TRANS) * (int)sizeof(float2);
+    constexpr int smem = contig_smem_elems(N, E, P, TRANS) * (int)sizeof(float2);
     auto kern = contig_kernel<N, E, P, S, TRANS>;
     static cudaError_t attr = set_smem(kern, smem);
     if (attr != cudaSuccess) return attr;
@@ -30,11 +29,10 @@ cudaError_t launch_contig(const void *in, void *out, const PassArgs &a, cudaStre
     return cudaGetLastError();
 }
 
-template <int N, int E, class S, bool TWID>
+template <int N, int E, int W, class S, bool TWID>
 cudaError_t launch_strided(const void *in, void *out, const PassArgs &a, cudaStream_t st) {
     constexpr int T = N / E;
-    constexpr int W = strided_W(N, E);
-    constexpr int smem = strided_smem_elems(N, E) * (int)sizeof(float2);
+    constexpr int smem = strided_smem_elems(N, E, W) * (int)sizeof(float2);
     auto kern = strided_kernel<N, E, W, S, TWID>;
     static cudaError_t attr = set_smem(kern, smem);
     if (attr != cudaSuccess) return attr;
@@ -45,24 +43,53 @@ cudaError_t launch_strided(const void *in, void *out, const PassArgs &a, cudaStr
     return cudaGetLastError();
 }
 
+// default tile shape for (N, E)
 template <int N, int E, class S>
 cudaError_t launch_n(int kind, bool variant, const void *in, void *out, const PassArgs &a,
                      cudaStream_t st) {
     if (kind == PASS_CONTIG) {
-        if (!variant) return launch_contig<N, E, S, false>(in, out, a, st);
-        if constexpr (N >= 64) return launch_contig<N, E, S, true>(in, out, a, st);
+        if (!variant) return launch_contig<N, E, contig_P(N, E, false), S, false>(in, out, a, st);
+        if constexpr (N >= 64) return launch_contig<N, E, contig_P(N, E, true), S, true>(in, out, a, st);
     } else {
-        if (!variant) return launch_strided<N, E, S, false>(in, out, a, st);
-        if constexpr (N >= 64) return launch_strided<N, E, S, true>(in, out, a, st);
+        if (!variant) return launch_strided<N, E, strided_W(N, E), S, false>(in, out, a, st);
+        if constexpr (N >= 64) return launch_strided<N, E, strided_W(N, E), S, true>(in, out, a, st);
     }
+    return cudaErrorInvalidValue;
+}
+
+// Extra (E, tile) shapes for the autotuner: plain (non-variant) passes only.
+// tile = P for the contiguous axis, W for strided axes.
+template <class S>
+cudaError_t launch_extra(int kind, int N, int E, int tile, const void *in, void *out,
+                         const PassArgs &a, cudaStream_t st) {
+#define WSFFT_XC(n, e, t) \
+    if (kind == PASS_CONTIG && N == n && E == e && tile == t) return launch_contig<n, e, t, S, false>(in, out, a, st);
+#define WSFFT_XS(n, e, t) \
+    if (kind == PASS_STRIDED && N == n && E == e && tile == t) return launch_strided<n, e, t, S, false>(in, out, a, st);
+    WSFFT_XS(512, 16, 16)
+    WSFFT_XS(512, 8, 8)
+    WSFFT_XS(512, 16, 8)
+    WSFFT_XS(512, 16, 32)
+    WSFFT_XS(256, 16, 32)
+    WSFFT_XS(256, 8, 16)
+    WSFFT_XS(1024, 16, 8)
+    WSFFT_XC(512, 16, 8)
+    WSFFT_XC(512, 8, 8)
+    WSFFT_XC(256, 8, 8)
+#undef WSFFT_XC
+#undef WSFFT_XS
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t WSFFT_LAUNCH_NAME(int kind, int N, int E, bool variant, const void *in, void *out,
-                              const PassArgs &a, cudaStream_t st) {
+cudaError_t WSFFT_LAUNCH_NAME(int kind, int N, int E, int tile, bool variant, const void *in,
+                              void *out, const PassArgs &a, cudaStream_t st) {
     using S = WSFFT_STORE;
+    if (tile > 0) {
+        if (variant) return cudaErrorInvalidValue;
+        return launch_extra<S>(kind, N, E, tile, in, out, a, st);
+    }
 #define WSFFT_CASE(n)                                                              \
     case n:                                                                        \
         if (E == default_E(n)) return launch_n<n, default_E(n), S>(kind, variant, in, out, a, st); \

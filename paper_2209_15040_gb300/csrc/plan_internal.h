@@ -17,6 +17,7 @@ enum { DST_OUT = 0, DST_WORK = 1 };
 struct PassSpec {
     int kind;                    // PassKind
     int N, E;                    // axis length, values per thread
+    int tile;                    // 0 = default tile shape, else pencils per block
     bool variant;                // contiguous: transposed store; strided: four-step twiddle
     int64_t inner;               // element stride along the axis
     int64_t npencils_per_batch;  // pencils per transform
@@ -27,6 +28,11 @@ struct PassSpec {
     int64_t trans_rows;          // transposed store: rows per transform
     int64_t twid_len;            // four-step twiddle: length of the long axis
     const float2 *tw;            // device stage-twiddle table
+    // persistent engine passes (kind PASS_ENGINE_A / PASS_ENGINE_B)
+    const void *items;           // device item table
+    int nitems;
+    int64_t units;               // completion counters used (pass A)
+    float c_scale, s_scale;      // pass A: scale after the contiguous / strided superstep
 };
 
 struct Plan {
@@ -37,6 +43,7 @@ struct Plan {
     int64_t elems = 1;  // per transform
     int dtype = 0, dir = -1, norm = 0;
     std::vector<PassSpec> passes;
+    std::map<int, std::pair<int, int>> overrides;  // pass index -> (E, tile)
     std::map<std::pair<int, int>, float2 *> tables;
     int64_t chunk = 1;        // transforms per workspace-sized chunk
     int64_t work_elems = 0;   // workspace elements needed by the schedule
@@ -44,11 +51,22 @@ struct Plan {
     void *work = nullptr;
     void *host_buf = nullptr;  // device buffer for wsfft_execute_host
     int *d_status = nullptr;   // device status word (timeouts)
+    // persistent engine state
+    int sm_count = 0;
+    int eng_grid = 0;
+    int engine_mode = 0;           // 0 one launch per superstep, 1 persistent, 2 pipelined, 3 warp-per-pencil
+    int persist_grid = 0;          // persistent kernel blocks (all resident)
+    void *d_items = nullptr;       // item tables of passes A and B
+    uint32_t *d_ctr = nullptr;     // ticket and completion counters
+    int64_t ctr_cap = 0;
+    int64_t wait_timeout_ns = 1000000000;  // 1 s per bounded wait
+    bool withhold = false;         // testing: drop one completion signal
     std::vector<cudaEvent_t> prof_ev;  // 2 per launch slot when profiling
     int prof_used = 0;                 // launch slots recorded since the last read
 
     const float2 *table(int N, int E);
     int build_schedule();
+    int build_engine(int64_t n, bool inv);
     int run(const void *in, void *out, cudaStream_t st);
     // bracket one kernel launch with profiling events (no-op when off)
     void prof_begin(cudaStream_t st);

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -29,6 +30,8 @@
 #include "fft_core.cuh"
 #include "pass_desc.h"
 #include "pass_kernels.cuh"
+#include "engine.cuh"
+#include "engine_desc.h"
 #include "plan_internal.h"
 
 using namespace wsfft;
@@ -96,12 +99,45 @@ float axis_scale(int64_t n, int dir, int norm) {
     return 1.f;
 }
 
+cudaError_t launch_engine(int dtype, int n, const EngArgs &a, int grid, cudaStream_t st) {
+    switch (dtype) {
+        case WSFFT_C32: return launch_engine_c32(n, a, grid, st);
+        case WSFFT_C16F: return launch_engine_c16f(n, a, grid, st);
+        default: return launch_engine_c16bf(n, a, grid, st);
+    }
+}
+
+cudaError_t launch_persist(int dtype, int n, const EngArgs &a, int s_mode, int *per_sm, int grid,
+                           cudaStream_t st) {
+    switch (dtype) {
+        case WSFFT_C32: return launch_persist_c32(n, a, s_mode, per_sm, grid, st);
+        case WSFFT_C16F: return launch_persist_c16f(n, a, s_mode, per_sm, grid, st);
+        default: return launch_persist_c16bf(n, a, s_mode, per_sm, grid, st);
+    }
+}
+
+cudaError_t launch_wpp(int dtype, int n, const EngArgs &a, int *per_sm, int grid, cudaStream_t st) {
+    switch (dtype) {
+        case WSFFT_C32: return launch_wpp_c32(n, a, per_sm, grid, st);
+        case WSFFT_C16F: return launch_wpp_c16f(n, a, per_sm, grid, st);
+        default: return launch_wpp_c16bf(n, a, per_sm, grid, st);
+    }
+}
+
+cudaError_t launch_wps(int dtype, int n, const WpStridedArgs &b, cudaStream_t st) {
+    switch (dtype) {
+        case WSFFT_C32: return launch_wps_c32(n, b, st);
+        case WSFFT_C16F: return launch_wps_c16f(n, b, st);
+        default: return launch_wps_c16bf(n, b, st);
+    }
+}
+
 cudaError_t launch(int dtype, const PassSpec &p, const void *in, void *out, const PassArgs &a,
                    cudaStream_t st) {
     switch (dtype) {
-        case WSFFT_C32: return launch_pass_c32(p.kind, p.N, p.E, p.variant, in, out, a, st);
-        case WSFFT_C16F: return launch_pass_c16f(p.kind, p.N, p.E, p.variant, in, out, a, st);
-        default: return launch_pass_c16bf(p.kind, p.N, p.E, p.variant, in, out, a, st);
+        case WSFFT_C32: return launch_pass_c32(p.kind, p.N, p.E, p.tile, p.variant, in, out, a, st);
+        case WSFFT_C16F: return launch_pass_c16f(p.kind, p.N, p.E, p.tile, p.variant, in, out, a, st);
+        default: return launch_pass_c16bf(p.kind, p.N, p.E, p.tile, p.variant, in, out, a, st);
     }
 }
 
@@ -126,6 +162,132 @@ const float2 *Plan::table(int N, int E) {
     return d;
 }
 
+// Two-launch schedule of an n^3 cube on the persistent engine.
+// Pass A: per slab (fixed first index), the contiguous superstep (z) then the
+// strided superstep along the middle axis (y), queued `lag` slabs apart so
+// the slab is still in L2 when it is read again.  Pass B: the superstep along
+// the first axis (x).
+int Plan::build_engine(int64_t n, bool inv) {
+    int grid = eng_grid;
+    if (engine_mode == 1 || engine_mode == 3) {
+        int per_sm = 0;
+        EngArgs dummy{};
+        cudaError_t e = engine_mode == 1 ? launch_persist(dtype, (int)n, dummy, 0, &per_sm, 0, 0)
+                                         : launch_wpp(dtype, (int)n, dummy, &per_sm, 0, 0);
+        if (e != cudaSuccess || per_sm < 1) return WSFFT_ERR_UNSUPPORTED;
+        persist_grid = per_sm * sm_count;
+        grid = persist_grid;
+    }
+    // pencils per contiguous tile (tp) and per strided tile (tq)
+    int64_t tp, tq;
+    if (engine_mode == 3) {
+        tp = wp_tile_z((int)n);
+        tq = wp_tile_y((int)n);
+    } else {
+        tp = (engine_mode == 1 && n == 512) ? 8 : engine_tile_pencils((int)n);
+        tq = tp;
+    }
+    const int64_t zper = n / tp, yper = n / tq;       // tiles per slab of each kind
+    const int64_t U = batch * n;                      // slabs
+    if (U * (zper + yper) > (int64_t)1 << 30) return WSFFT_ERR_UNSUPPORTED;
+    const int64_t window = engine_mode == 2 ? 3 * (int64_t)grid : 2 * (int64_t)grid;  // tiles held
+    int64_t lag = (window + zper + yper - 1) / (zper + yper) + 2;
+    if (lag > U) lag = U;
+    std::vector<EngItem> items;
+    items.reserve((size_t)(U * (zper + yper) + batch * n * n / tq));
+    for (int64_t j = 0; j < U + lag; ++j) {
+        if (j < U)
+            for (int64_t t = 0; t < zper; ++t)
+                items.push_back(EngItem{ITEM_SIGNAL, (int)j, (int)t, 0});
+        if (j >= lag)
+            for (int64_t t = 0; t < yper; ++t)
+                items.push_back(EngItem{ITEM_STRIDED | ITEM_WAIT, (int)(j - lag), (int)t, 0});
+    }
+    if (withhold) items[0].flags &= ~ITEM_SIGNAL;
+    const int na = (int)items.size();
+    if (engine_mode == 2)
+        for (int64_t b = 0; b < batch; ++b)
+            for (int64_t t = 0; t < n * n / tq; ++t) items.push_back(EngItem{ITEM_STRIDED, (int)b, (int)t, 0});
+    const int nb = (int)items.size() - na;
+    if (d_items) cudaFree(d_items);
+    d_items = nullptr;
+    if (cudaMalloc(&d_items, items.size() * sizeof(EngItem)) != cudaSuccess) {
+        d_items = nullptr;
+        return WSFFT_ERR_ALLOC;
+    }
+    if (cudaMemcpy(d_items, items.data(), items.size() * sizeof(EngItem), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return WSFFT_ERR_CUDA;
+    if (1 + U > ctr_cap) {
+        if (d_ctr) cudaFree(d_ctr);
+        d_ctr = nullptr;
+        ctr_cap = 0;
+        if (cudaMalloc(&d_ctr, (size_t)(1 + U) * sizeof(uint32_t)) != cudaSuccess) {
+            d_ctr = nullptr;
+            return WSFFT_ERR_ALLOC;
+        }
+        ctr_cap = 1 + U;
+    }
+    const float sc = axis_scale(n, dir, norm);
+    PassSpec a{};
+    a.kind = engine_mode == 1 ? PASS_PERSIST_A : engine_mode == 3 ? PASS_WP_A : PASS_ENGINE_A;
+    a.N = (int)n;
+    a.E = engine_mode == 1 && n == 512 ? 8 : 16;
+    a.tile = (int)tp;
+    a.trans_rows = zper;  // completion target of a slab
+    a.items = d_items;
+    a.nitems = na;
+    a.units = U;
+    a.conj_in = inv;
+    a.c_scale = sc;
+    a.s_scale = sc;
+    a.transform_elems = n * n * n;
+    PassSpec b{};
+    if (engine_mode == 3) {
+        b.kind = PASS_WP_B;
+        b.N = (int)n;
+        b.E = 16;
+        b.inner = n * n;
+        b.npencils_per_batch = n * n;
+        b.src = SRC_OUT;
+        b.dst = DST_OUT;
+    } else if (engine_mode == 2) {
+        b.kind = PASS_ENGINE_B;
+        b.N = (int)n;
+        b.E = 16;
+        b.items = (const EngItem *)d_items + na;
+        b.nitems = nb;
+        b.units = 0;
+    } else {
+        // x: one launch of the strided superstep kernel (512: 16 values per
+        // thread, 16 pencils of 128-byte rows per block)
+        b.kind = PASS_STRIDED;
+        b.N = (int)n;
+        b.E = n == 512 ? 16 : default_E((int)n);
+        b.tile = n == 512 ? 16 : 0;
+        b.inner = n * n;
+        b.npencils_per_batch = n * n;
+        b.src = SRC_OUT;
+        b.dst = DST_OUT;
+    }
+    b.conj_out = inv;
+    b.scale = sc;
+    b.transform_elems = n * n * n;
+    passes.push_back(a);
+    passes.push_back(b);
+    for (auto &kv : overrides) {
+        if (kv.first < (int)passes.size() && passes[kv.first].kind == PASS_STRIDED) {
+            passes[kv.first].E = kv.second.first;
+            passes[kv.first].tile = kv.second.second;
+        }
+    }
+    for (auto &p : passes) {
+        p.tw = table(p.N, p.E);
+        if (!p.tw) return WSFFT_ERR_ALLOC;
+    }
+    return WSFFT_SUCCESS;
+}
+
 // (Re)build the pass list from shape, direction and normalisation.
 int Plan::build_schedule() {
     passes.clear();
@@ -138,6 +300,10 @@ int Plan::build_schedule() {
     work_elems = 0;
     chunk = batch;
 
+    if (r == 3 && engine_mode != 0 && d[0] == d[1] && d[1] == d[2] && engine_supports((int)d[0]) &&
+        (engine_mode != 3 || wp_supports((int)d[0])) && eng_grid > 0) {
+        return build_engine(d[0], inv);
+    }
     if (r == 1 && d[0] > 4096) {
         const int64_t n = d[0];
         const int lg = ilog2(n);
@@ -189,6 +355,12 @@ int Plan::build_schedule() {
             p.N = (int)d[ax];
             p.E = default_E(p.N);
             p.variant = false;
+            if (p.kind == PASS_STRIDED && p.N == 512 && inner % 16 == 0) {
+                // measured: 16 values per thread, 16 pencils of 128-byte rows
+                // per 512-thread block beats the 1024-thread default shape
+                p.E = 16;
+                p.tile = 16;
+            }
             p.inner = inner;
             p.npencils_per_batch = total / d[ax];
             p.src = ax == r - 1 ? SRC_IN : SRC_OUT;
@@ -198,6 +370,13 @@ int Plan::build_schedule() {
             p.scale = axis_scale(d[ax], dir, norm);
             p.transform_elems = total;
             passes.push_back(p);
+        }
+    }
+    for (auto &kv : overrides) {
+        if (kv.first < (int)passes.size() && !passes[kv.first].variant &&
+            (passes[kv.first].kind == PASS_CONTIG || passes[kv.first].kind == PASS_STRIDED)) {
+            passes[kv.first].E = kv.second.first;
+            passes[kv.first].tile = kv.second.second;
         }
     }
     for (auto &p : passes) {
@@ -223,6 +402,68 @@ int Plan::run(const void *in, void *out, cudaStream_t st) {
     for (int64_t b0 = 0; b0 < batch; b0 += chunk) {
         const int64_t nb = std::min(chunk, batch - b0);
         for (const auto &p : passes) {
+            if (p.kind == PASS_WP_B) {
+                WpStridedArgs b{};
+                b.in = out;
+                b.out = out;
+                b.inner = p.inner;
+                b.log_inner = ilog2(p.inner);
+                b.npencils = p.npencils_per_batch * batch;
+                b.tw = p.tw;
+                b.ci = 1.f;
+                b.sx = p.scale;
+                b.sy = p.conj_out ? -p.scale : p.scale;
+                prof_begin(st);
+                cudaError_t err = launch_wps(dtype, p.N, b, st);
+                prof_end(st);
+                if (err != cudaSuccess) return err == cudaErrorInvalidValue ? WSFFT_ERR_UNSUPPORTED : WSFFT_ERR_CUDA;
+                continue;
+            }
+            if (p.kind == PASS_ENGINE_A || p.kind == PASS_ENGINE_B || p.kind == PASS_PERSIST_A ||
+                p.kind == PASS_WP_A) {
+                EngArgs e{};
+                e.items = (const EngItem *)p.items;
+                e.nitems = p.nitems;
+                e.ctr = d_ctr;
+                e.status = d_status;
+                e.tw_c = p.tw;
+                e.tw_s = p.tw;
+                e.timeout_ns = (uint64_t)wait_timeout_ns;
+                const int64_t n = p.N;
+                if (p.kind == PASS_ENGINE_A || p.kind == PASS_PERSIST_A || p.kind == PASS_WP_A) {
+                    e.c_src = in;
+                    e.c_dst = out;
+                    e.s_src = out;
+                    e.s_dst = out;
+                    e.unit_elems = n * n;
+                    e.s_stride = n;
+                    e.c_ci = p.conj_in ? -1.f : 1.f;
+                    e.c_sx = e.c_sy = p.c_scale;
+                    e.s_ci = 1.f;
+                    e.s_sx = e.s_sy = p.s_scale;
+                    e.dep_target = (uint32_t)p.trans_rows;
+                    e.s_evict_first = 0;
+                } else {
+                    e.s_src = out;
+                    e.s_dst = out;
+                    e.unit_elems = n * n * n;
+                    e.s_stride = n * n;
+                    e.s_ci = 1.f;
+                    e.s_sx = p.scale;
+                    e.s_sy = p.conj_out ? -p.scale : p.scale;
+                    e.s_evict_first = 1;
+                }
+                if (cudaMemsetAsync(d_ctr, 0, (size_t)(1 + p.units) * sizeof(uint32_t), st) != cudaSuccess)
+                    return WSFFT_ERR_CUDA;
+                prof_begin(st);
+                cudaError_t err = p.kind == PASS_PERSIST_A
+                                      ? launch_persist(dtype, p.N, e, 0, nullptr, persist_grid, st)
+                                  : p.kind == PASS_WP_A ? launch_wpp(dtype, p.N, e, nullptr, persist_grid, st)
+                                                        : launch_engine(dtype, p.N, e, eng_grid, st);
+                prof_end(st);
+                if (err != cudaSuccess) return err == cudaErrorInvalidValue ? WSFFT_ERR_UNSUPPORTED : WSFFT_ERR_CUDA;
+                continue;
+            }
             const int64_t off = b0 * p.transform_elems * eb;
             const char *src = p.src == SRC_IN ? (const char *)in + off
                               : p.src == SRC_OUT ? (const char *)out + off
@@ -261,6 +502,8 @@ void Plan::prof_end(cudaStream_t st) {
 
 Plan::~Plan() {
     for (auto e : prof_ev) cudaEventDestroy(e);
+    if (d_items) cudaFree(d_items);
+    if (d_ctr) cudaFree(d_ctr);
     for (auto &kv : tables) cudaFree(kv.second);
     if (work) cudaFree(work);
     if (host_buf) cudaFree(host_buf);
@@ -304,6 +547,12 @@ int wsfft_plan_create(wsfft_plan *plan, const int64_t *dims, int rank, int dtype
     }
     p->rank = rank;
     for (int i = 0; i < rank; ++i) p->dims[i] = dims[i];
+    cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    p->eng_grid = p->sm_count;  // one engine block per SM (its shared memory fills the SM)
+    {
+        const char *env = getenv("WSFFT_ENGINE");
+        if (env && env[0] >= '0' && env[0] <= '3') p->engine_mode = env[0] - '0';
+    }
     p->dtype = dtype;
     p->dir = direction;
     p->batch = batch;
@@ -374,6 +623,47 @@ int wsfft_destroy(wsfft_plan plan) {
     delete p;
     if (prev >= 0 && prev != dev) cudaSetDevice(prev);
     return cuda_status(e);
+}
+
+int wsfft_plan_set_pass_variant(wsfft_plan plan, int pass, int values_per_thread, int tile) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || pass < 0 || pass >= (int)p->passes.size() || values_per_thread < 0 || tile < 0)
+        return WSFFT_ERR_INVALID_ARG;
+    if (values_per_thread == 0 && tile == 0) {
+        p->overrides.erase(pass);
+        return p->build_schedule();
+    }
+    const PassSpec &ps = p->passes[pass];
+    if (ps.variant || (ps.kind != PASS_CONTIG && ps.kind != PASS_STRIDED)) return WSFFT_ERR_UNSUPPORTED;
+    // probe: is this shape instantiated?  (an empty launch returns before running)
+    PassArgs a{};
+    a.npencils = 0;
+    PassSpec probe = ps;
+    probe.E = values_per_thread;
+    probe.tile = tile;
+    if (launch(p->dtype, probe, nullptr, nullptr, a, 0) == cudaErrorInvalidValue)
+        return WSFFT_ERR_UNSUPPORTED;
+    p->overrides[pass] = std::make_pair(values_per_thread, tile);
+    return p->build_schedule();
+}
+
+int wsfft_plan_set_engine(wsfft_plan plan, int mode) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || mode < 0 || mode > 3) return WSFFT_ERR_INVALID_ARG;
+    p->engine_mode = mode;
+    return p->build_schedule();
+}
+
+int wsfft_plan_set_wait_test(wsfft_plan plan, int withhold, int64_t timeout_ns) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || timeout_ns <= 0) return WSFFT_ERR_INVALID_ARG;
+    bool uses_engine = false;
+    for (auto &ps : p->passes)
+        uses_engine |= ps.kind == PASS_ENGINE_A || ps.kind == PASS_PERSIST_A || ps.kind == PASS_WP_A;
+    if (!uses_engine) return WSFFT_ERR_UNSUPPORTED;
+    p->withhold = withhold != 0;
+    p->wait_timeout_ns = timeout_ns;
+    return p->build_schedule();
 }
 
 int wsfft_plan_sync_status(wsfft_plan plan, wsfft_stream stream) {

@@ -39,6 +39,7 @@ EXPORTS = (
     "wsfft_plan_create", "wsfft_plan_set_norm", "wsfft_execute", "wsfft_execute_host",
     "wsfft_destroy", "wsfft_plan_create_ragged", "wsfft_execute_ragged", "wsfft_autotune",
     "wsfft_plan_sync_status", "wsfft_plan_passes", "wsfft_plan_profile",
+    "wsfft_plan_set_pass_variant", "wsfft_plan_set_engine", "wsfft_plan_set_wait_test",
     "wsfft_plan_launch_times", "wsfft_status_string",
 )
 
@@ -73,6 +74,9 @@ def lib():
         L.wsfft_plan_sync_status.argtypes = [P, P]
         L.wsfft_plan_passes.argtypes = [P, ctypes.POINTER(ci), ctypes.POINTER(i64)]
         L.wsfft_plan_profile.argtypes = [P, ci]
+        L.wsfft_plan_set_pass_variant.argtypes = [P, ci, ci, ci]
+        L.wsfft_plan_set_engine.argtypes = [P, ci]
+        L.wsfft_plan_set_wait_test.argtypes = [P, ci, i64]
         L.wsfft_plan_launch_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), ci,
                                               ctypes.POINTER(ci)]
         L.wsfft_status_string.argtypes = [ci]
@@ -146,6 +150,21 @@ class Plan:
         _check(lib().wsfft_plan_passes(self._h, ctypes.byref(n), ctypes.byref(b)),
                "wsfft_plan_passes")
         return n.value, b.value
+
+    def set_pass_variant(self, pass_index: int, values_per_thread: int, tile: int) -> None:
+        """Kernel shape of one pass (0, 0 = default); see wsfft_plan_set_pass_variant."""
+        _check(lib().wsfft_plan_set_pass_variant(self._h, int(pass_index), int(values_per_thread),
+                                                 int(tile)), "wsfft_plan_set_pass_variant")
+
+    def set_engine(self, mode) -> None:
+        """Cube schedule: 0 one launch per superstep (default), 3 warp-per-pencil,
+        1 persistent, 2 pipelined."""
+        _check(lib().wsfft_plan_set_engine(self._h, int(mode)), "wsfft_plan_set_engine")
+
+    def set_wait_test(self, withhold: bool, timeout_ns: int) -> None:
+        """Testing aid: drop one completion signal so bounded waits run out."""
+        _check(lib().wsfft_plan_set_wait_test(self._h, int(bool(withhold)), int(timeout_ns)),
+               "wsfft_plan_set_wait_test")
 
     def profile(self, capacity: int) -> None:
         """Record CUDA events around up to ``capacity`` later kernel launches."""

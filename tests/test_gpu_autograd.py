@@ -52,8 +52,11 @@ def test_grad_16cubed_vs_oracle_and_finite_differences():
             xm[i] -= h * part
             fd = (oracle.loss(xp.reshape(shape), w64) - oracle.loss(xm.reshape(shape), w64)) / (2 * h)
             an = g.ravel()[i].real if part == 1.0 else g.ravel()[i].imag
-            errs.append(abs(fd - an) / max(1.0, abs(fd)))
-    assert max(errs) < 1e-5, max(errs)
+            errs.append(abs(fd - an))
+    # pointwise error against the gradient's RMS: FP32 rounding of the GPU
+    # path is ~1e-7 of that scale, the FD rounding ~eps*L/h smaller still
+    rms = float(np.sqrt(np.mean(np.abs(g_ref) ** 2)))
+    assert max(errs) < 1e-5 * rms, (max(errs), rms)
 
 
 def test_grad_batch8_128cubed():

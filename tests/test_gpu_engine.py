@@ -1,0 +1,141 @@
+"""GPU parity of the n^3 cube schedules -- one launch per superstep (the
+default) and the two-launch schedules that fuse the supersteps along the two
+inner axes per slab through L2 -- at sizes up to the 512^3 benchmark
+configuration, plus the bounded-wait failure path of the fused schedules."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_15040_gb300 import build, inputs
+from paper_2209_15040_gb300 import wsfft as W
+from tests._helpers import DT, TOL, seeded, to_device, to_host_c128
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build_library()
+    W.lib()
+
+
+def run(x_dev, dims, dtype, direction, batch=1, norm=None, engine=None, inplace=False):
+    plan = W.Plan(dims, DT[dtype], direction, batch, norm)
+    if engine is not None:
+        plan.set_engine(engine)
+    npass, _ = plan.passes()
+    out = x_dev if inplace else torch.empty_like(x_dev)
+    plan.execute(x_dev.data_ptr(), out.data_ptr())
+    torch.cuda.synchronize()
+    assert plan.sync_status() == W.SUCCESS
+    plan.close()
+    return out, npass
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("n", [128, 256])
+@pytest.mark.parametrize("direction", [W.FORWARD, W.INVERSE])
+def test_engine_cube_c32(n, direction, mode):
+    xs, xc = seeded((n, n, n), 1, "normal", "c32")
+    y, npass = run(to_device(xs, "c32"), (n, n, n), "c32", direction, engine=mode)
+    assert npass == 2
+    ref = oracle.fftn(xc, sign=direction)
+    err = oracle.rel_l2(to_host_c128(y, "c32"), ref)
+    print(f"engine {n}^3 dir {direction}: rel_l2 {err:.3e}")
+    assert err < TOL["c32"]
+
+
+@pytest.mark.parametrize("n", [128, 512])
+def test_engine_matches_superstep_schedule(n):
+    batch = 2 if n == 128 else 1
+    xs, _ = seeded((batch, n, n, n), 3, "normal", "c32")
+    x = to_device(xs, "c32")
+    ref = oracle.fftn(xs.astype(np.complex128), rank=3)
+    outs = {}
+    for mode, want in ((3, 2), (1, 2), (2, 2), (0, 3)):
+        y, npass = run(x, (n, n, n), "c32", W.FORWARD, batch=batch, engine=mode)
+        assert npass == want
+        outs[mode] = to_host_c128(y, "c32")
+        del y
+        assert oracle.rel_l2(outs[mode], ref) < TOL["c32"]
+    assert oracle.rel_l2(outs[1], outs[0]) < 2e-6
+
+
+def test_engine_in_place_and_batched():
+    n = 128
+    xs, xc = seeded((3, n, n, n), 4, "normal", "c32")
+    y, _ = run(to_device(xs, "c32"), (n, n, n), "c32", W.INVERSE, batch=3, inplace=True)
+    ref = oracle.fftn(xc, rank=3, sign=+1)
+    assert oracle.rel_l2(to_host_c128(y, "c32"), ref) < TOL["c32"]
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("dtype", ["c16f", "c16bf"])
+@pytest.mark.parametrize("n", [128, 256])
+def test_engine_half_storage(dtype, n, mode):
+    xs, xc = seeded((n, n, n), 0, "uniform", dtype)
+    y, npass = run(to_device(xs, dtype), (n, n, n), dtype, W.FORWARD, engine=mode)
+    assert npass == 2
+    ref = oracle.fftn(xc, norm=oracle.NORM_ORTHO)
+    err = oracle.rel_l2(to_host_c128(y, dtype), ref)
+    print(f"engine {n}^3 {dtype}: rel_l2 {err:.3e}")
+    assert err < TOL[dtype]
+
+
+# -- the benchmark configuration at full size ----------------------------------
+
+@pytest.mark.parametrize("direction,mode", [(W.FORWARD, None), (W.INVERSE, None), (W.FORWARD, 3)])
+def test_512cubed_full_size(direction, mode):
+    # mode None: the plan's default schedule, the one bench.py times
+    n = 512
+    xs, xc = seeded((n, n, n), 1, "normal", "c32")
+    y, npass = run(to_device(xs, "c32"), (n, n, n), "c32", direction, engine=mode)
+    assert npass == (3 if mode is None else 2)
+    got = to_host_c128(y, "c32")
+    del y
+    ref = oracle.fftn(xc, sign=direction)
+    err = oracle.rel_l2(got, ref)
+    print(f"512^3 dir {direction}: rel_l2 {err:.3e} max_abs {oracle.max_abs(got, ref):.3e}")
+    assert err < TOL["c32"]
+    # sampled coefficients by direct O(N) summation, independent of the FFT
+    if direction == W.FORWARD:
+        k = np.array([0, 1, 513, 262145, 134217727, 77777777])
+        pts = oracle.dft_points(xc, k)
+        assert np.max(np.abs(got.ravel()[k] - pts)) < 1e-5 * np.sqrt(n ** 3)
+
+
+@pytest.mark.parametrize("dtype", ["c16f", "c16bf"])
+def test_512cubed_half_storage(dtype):
+    n = 512
+    xs, xc = seeded((n, n, n), 0, "uniform", dtype)
+    y, _ = run(to_device(xs, dtype), (n, n, n), dtype, W.FORWARD)
+    got = to_host_c128(y, dtype)
+    del y
+    ref = oracle.fftn(xc, norm=oracle.NORM_ORTHO)
+    err = oracle.rel_l2(got, ref)
+    print(f"512^3 {dtype}: rel_l2 {err:.3e} max_abs {oracle.max_abs(got, ref):.3e}")
+    assert err < TOL[dtype]
+
+
+# -- bounded waits ---------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_withheld_signal_times_out_and_plan_recovers(mode):
+    n = 128
+    xs, xc = seeded((n, n, n), 5, "normal", "c32")
+    x = to_device(xs, "c32")
+    y = torch.empty_like(x)
+    plan = W.Plan((n, n, n), W.C32, W.FORWARD, 1)
+    plan.set_engine(mode)
+    assert plan.passes()[0] == 2
+    plan.set_wait_test(True, 20_000_000)  # 20 ms per wait
+    plan.execute(x.data_ptr(), y.data_ptr())
+    assert plan.sync_status() == W.ERR_DEVICE_TIMEOUT
+    assert plan.sync_status() == W.SUCCESS  # cleared once reported
+    # the context is still usable and the plan works again
+    plan.set_wait_test(False, 1_000_000_000)
+    plan.execute(x.data_ptr(), y.data_ptr())
+    assert plan.sync_status() == W.SUCCESS
+    assert oracle.rel_l2(to_host_c128(y, "c32"), oracle.fftn(xc)) < TOL["c32"]
+    plan.close()
