@@ -200,6 +200,28 @@ int wsfft_plan_profile(wsfft_plan plan, int capacity);
  * to only reset.  Errors: INVALID_ARG, CUDA. */
 int wsfft_plan_launch_times(wsfft_plan plan, float *ms, int capacity, int *count);
 
+/* Allocation-free n^3 transform (the paper has no counterpart: it is an
+ * interface for callers that cannot allocate device memory -- code that runs
+ * while a CUDA graph is being captured, code whose device memory is owned by
+ * another framework's allocator, or programs that reserve all device memory
+ * up front).  Computes the same transform as a complex64 plan of dims
+ * (n, n, n), `batch` transforms, in `direction`, with WSFFT_NORM_PAPER, from
+ * device pointer `in` to device pointer `out` (16-byte aligned; in == out
+ * allowed) on `stream`, and calls no cudaMalloc or cudaFree: its scratch
+ * counters (16 KiB) and twiddle tables (16 KiB) live in static device arrays
+ * that every GPU loading the library keeps until the process exits.
+ *   n: 128, 256 or 512; batch * n <= 4096.  Larger sizes return
+ *   WSFFT_ERR_INVALID_SIZE; null or misaligned pointers and bad directions
+ *   return WSFFT_ERR_INVALID_ARG.
+ * The first call on each device does that device's set-up (table upload,
+ * symbol lookup, occupancy query) with the device current; make it before
+ * any stream capture.  All calls on a device share the scratch array, which
+ * keeps the last call's contents (each call clears the counters it uses):
+ * calls that overlap on the GPU race and must not be made.
+ * Errors: INVALID_ARG, INVALID_SIZE, UNSUPPORTED, CUDA. */
+int wsfft_execute_cube_noalloc(const void *in, void *out, int64_t n, int64_t batch,
+                               int direction, wsfft_stream stream);
+
 /* Static text for a status code. */
 const char *wsfft_status_string(int status);
 
