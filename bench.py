@@ -188,6 +188,63 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def ragged_leg(W, dev, stream, reps=5):
+    """The ragged configuration (256 uneven 3D shapes from seed 4, N(0,1)):
+    one persistent launch replayed from a captured CUDA graph vs one plan
+    execute per instance (3 launches each)."""
+    from paper_2209_15040_gb300 import inputs
+    shapes = inputs.ragged_shapes(256, 4)
+    g = torch.Generator(device=dev)
+    xs, ys = [], []
+    for i, s in enumerate(shapes):
+        g.manual_seed(1000 + i)
+        xs.append(torch.view_as_complex(torch.randn(tuple(int(v) for v in s) + (2,), generator=g,
+                                                    device=dev)).contiguous())
+        ys.append(torch.empty_like(xs[-1]))
+    elems = int(sum(int(np.prod(s)) for s in shapes))
+    ins, outs = [x.data_ptr() for x in xs], [y.data_ptr() for y in ys]
+    plan = W.RaggedPlan(shapes, W.C32, W.FORWARD)
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        plan.execute(ins, outs, side)
+        side.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            plan.execute(ins, outs, torch.cuda.current_stream())
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / reps * 1e3
+    plans = [W.Plan(tuple(int(v) for v in s), W.C32, W.FORWARD, 1) for s in shapes]
+    launches = sum(p.passes()[0] for p in plans)
+    def per_instance():
+        for p, i, o in zip(plans, ins, outs):
+            p.execute(i, o, stream)
+    for _ in range(2):
+        per_instance()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        per_instance()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_inst = e0.elapsed_time(e1) / reps * 1e3
+    for p in plans:
+        p.close()
+    plan.close()
+    return {"instances": len(shapes), "elements": elems, "bytes": elems * 8,
+            "persistent_graph_us": round(t_graph, 1), "per_instance_us": round(t_inst, 1),
+            "speedup": round(t_inst / t_graph, 3), "launches_persistent": 1,
+            "launches_per_instance": launches,
+            "hbm_gbs_3pass_equiv": round(3 * 2 * elems * 8 / (t_graph * 1e-6) / 1e9, 1)}
+
+
 def timed_pairs(fwd, inv, x, y, steps, warmup, world, stream):
     for _ in range(warmup):
         fwd.execute(x.data_ptr(), y.data_ptr(), stream)
@@ -216,8 +273,11 @@ def main():
     ap.add_argument("--impl", default="wsfft", choices=["wsfft", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch leg")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.steps < 1:
+        ap.error("--steps must be >= 1")
     world, rank, local = dist_init()
 
     if args.impl == "reference":
@@ -330,6 +390,10 @@ def main():
                "h2d_bytes_per_step": 2 * ELEMS * 8, "d2h_bytes_per_step": 2 * ELEMS * 8,
                "steps": esteps, "entry": "wsfft_execute_host (pinned host buffers)"}
 
+    ragged = None
+    if not args.no_ragged:
+        ragged = ragged_leg(W, dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_sample_oracle()
@@ -365,6 +429,8 @@ def main():
         }
         if e2e:
             line["e2e"] = e2e
+        if ragged:
+            line["ragged_batch"] = ragged
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

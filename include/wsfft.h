@@ -130,15 +130,21 @@ int wsfft_execute_host(wsfft_plan plan, const void *host_in, void *host_out,
 int wsfft_destroy(wsfft_plan plan);
 
 /* Plan for `count` independent rank-3 transforms of uneven shapes
- * dims[3*i .. 3*i+2] (each axis a power of two, 2..4096), executed by one
- * persistent launch that pulls (instance, pass, tile) tasks from a queue.
- * Section 4.4 (more than one pencil per processor) generalised to one
- * processor per tile.  Errors: INVALID_ARG, INVALID_SIZE, ALLOC, CUDA. */
+ * dims[3*i .. 3*i+2] (each axis a power of two, 32..256), executed by one
+ * persistent launch that pulls (instance, superstep, tile) tasks from a
+ * queue; a superstep's tiles wait (bounded) until the previous superstep of
+ * the same instance is complete.  Section 4.4 (more than one pencil per
+ * processor) generalised to one thread block per tile.  Normalisation as
+ * wsfft_plan_create (PAPER for WSFFT_C32, ORTHO otherwise).  The launch and
+ * its table upload can be captured in a CUDA graph (the upload is skipped
+ * when the pointers are unchanged).
+ * Errors: INVALID_ARG, INVALID_SIZE, ALLOC, CUDA. */
 int wsfft_plan_create_ragged(wsfft_plan *plan, int count, const int64_t *dims,
                              int dtype, int direction);
 
 /* Enqueue a ragged plan: in[i], out[i] are device pointers for instance i
- * (host arrays of `count` pointers).  Errors: as wsfft_execute. */
+ * (host arrays of `count` pointers, 16-byte aligned; in[i] == out[i]
+ * allowed; instances must not overlap).  Errors: as wsfft_execute. */
 int wsfft_execute_ragged(wsfft_plan plan, const void *const *in, void *const *out,
                          wsfft_stream stream);
 

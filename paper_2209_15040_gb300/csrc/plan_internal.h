@@ -60,6 +60,17 @@ struct Plan {
     uint32_t *d_ctr = nullptr;     // ticket and completion counters
     int64_t ctr_cap = 0;
     int64_t wait_timeout_ns = 1000000000;  // 1 s per bounded wait
+    // ragged plans
+    bool ragged = false;
+    int rag_count = 0;
+    int rag_grid = 0;
+    int rag_nitems = 0;
+    void *rag_items = nullptr;      // device RagItem table
+    void *rag_inst = nullptr;       // device RagInst table
+    void *rag_inst_host = nullptr;  // pinned host copy (pointers filled per execute)
+    cudaEvent_t rag_copied = nullptr;
+    bool rag_uploaded = false;
+    const float2 *rag_tw[9] = {};
     bool withhold = false;         // testing: drop one completion signal
     std::vector<cudaEvent_t> prof_ev;  // 2 per launch slot when profiling
     int prof_used = 0;                 // launch slots recorded since the last read

@@ -1,0 +1,187 @@
+// Ragged batch: many independent 3D transforms of uneven shapes in one
+// persistent launch.
+//
+// The paper maps one problem onto an n x n processor mesh and notes that
+// several small problems could share the machine (Section 5.3 discussion of
+// many 32^3 transforms; Section 4.4 for several pencils per processor).  Here
+// every instance contributes three supersteps' worth of tiles to one queue:
+//   z tiles (contiguous axis, P whole pencils), signal the instance's z counter
+//   y tiles (middle axis, W adjacent pencils), wait for all z tiles, signal y
+//   x tiles (outer axis, W adjacent pencils), wait for all y tiles.
+// The queue interleaves instances (z of instance s, y of s-1, x of s-2), so
+// an instance is usually still in L2 when its next superstep reads it, and
+// a tile only ever waits for tiles with smaller tickets (deadlock-free with
+// any number of resident blocks).  Axis lengths 32..256 are dispatched at run
+// time inside the kernel; every tile kind uses the same 256 threads.
+#pragma once
+
+#include "engine.cuh"
+#include "pass_kernels.cuh"
+
+namespace wsfft {
+
+struct RagInst {
+    const void *in;
+    void *out;
+    int n[3];          // axis lengths, n[2] contiguous
+    int log_n2, log_n12;
+    int tiles[3];      // tiles of the z, y, x supersteps
+    float scale[3];    // store scale of the z, y, x supersteps
+    int pad;
+};
+
+struct RagItem {
+    int flags;     // ITEM_* of engine.cuh; bits 8..9: superstep (0 z, 1 y, 2 x)
+    int inst;
+    int tile;
+    int pad;
+};
+
+struct RagArgs {
+    const RagItem *items;
+    int nitems;
+    const RagInst *inst;
+    uint32_t *ctr;         // [0] tickets, [1 + 2*i] z done of instance i, [2 + 2*i] y done
+    int *status;
+    const float2 *tw[9];   // stage tables indexed by log2(N) - 1 .. (N = 2..512), per N
+    float ci;              // +1, or -1: conjugate on the z load (inverse)
+    float co;              // +1, or -1: conjugate on the x store (inverse)
+    uint64_t timeout_ns;
+};
+
+constexpr int RAG_THREADS = 256;
+
+__host__ __device__ constexpr int rag_E(int N) { return N <= 64 ? 8 : 16; }
+__host__ __device__ constexpr int rag_T(int N) { return N / rag_E(N); }
+__host__ __device__ constexpr int rag_P(int N) { return RAG_THREADS / rag_T(N); }  // z pencils per tile
+__host__ __device__ constexpr int rag_W(int N) { return RAG_THREADS / rag_T(N); }  // y/x pencils per tile
+__host__ __device__ constexpr int rag_smem_elems() {
+    // max over N in {32..256} of the contiguous and strided exchange buffers
+    return 4608;
+}
+static_assert(rag_P(32) * contig_PS(32) <= 4608 && rag_P(64) * contig_PS(64) <= 4608 &&
+                  rag_P(128) * contig_PS(128) <= 4608 && rag_P(256) * contig_PS(256) <= 4608,
+              "contiguous exchange fits");
+static_assert(32 * rag_W(32) * 17 / 16 <= 4608 && 64 * rag_W(64) * 17 / 16 <= 4608 &&
+                  128 * rag_W(128) * 17 / 16 <= 4608 && 256 * rag_W(256) * 17 / 16 <= 4608,
+              "strided exchange fits");
+
+template <int N, class S>
+__device__ __forceinline__ void rag_contig(const RagInst &I, int tile, const float2 *tw, float ci,
+                                           float sc, float2 *smem) {
+    constexpr int T = rag_T(N), P = rag_P(N);
+    const int t = threadIdx.x % T, p = threadIdx.x / T;
+    const int64_t npen = (int64_t)I.n[0] * I.n[1];
+    const int64_t q = (int64_t)tile * P + p;
+    ContigAcc<S, OP_DEF, OP_DEF> acc{reinterpret_cast<const S *>(I.in) + q * N,
+                                     reinterpret_cast<S *>(I.out) + q * N, smem + p * contig_PS(N), ci,
+                                     {sc, sc}, q < npen};
+    pencil_fft<N, rag_E(N)>(acc, t, tw);
+}
+
+// strided superstep along axis d (1: y, inner n2; 2: x, inner n1*n2), read
+// and written in `out` (L2-coherent loads: other blocks wrote it this launch)
+template <int N, class S>
+__device__ __forceinline__ void rag_strided(const RagInst &I, int d, int tile, const float2 *tw,
+                                            float sx, float sy, float2 *smem) {
+    constexpr int T = rag_T(N), W = rag_W(N);
+    const int w = threadIdx.x % W, t = threadIdx.x / W;
+    const int log_inner = d == 1 ? I.log_n2 : I.log_n12;
+    const int64_t inner = (int64_t)1 << log_inner;
+    const int64_t npen = d == 1 ? (int64_t)I.n[0] * I.n[2] : (int64_t)I.n[1] * I.n[2];
+    const int64_t q = (int64_t)tile * W + w;
+    const int64_t o = q >> log_inner, i = q & (inner - 1);
+    const int64_t base = o * ((int64_t)N << log_inner) + i;
+    StridedAcc<S, false, OP_CG, OP_DEF> acc;
+    acc.in = reinterpret_cast<const S *>(I.out) + base;
+    acc.out = reinterpret_cast<S *>(I.out) + base;
+    acc.sm = smem;
+    acc.stride = inner;
+    acc.w = w;
+    acc.W = W;
+    acc.ci = 1.f;
+    acc.epi = Epi{sx, sy};
+    acc.active = q < npen;
+    acc.twq = 0;
+    acc.tw_inv = 0.f;
+    acc.tw_mask = 0;
+    (void)T;
+    pencil_fft<N, rag_E(N)>(acc, t, tw);
+}
+
+template <class S>
+__device__ __forceinline__ void rag_tile(const RagArgs &a, const RagInst &I, int d, int tile,
+                                         float2 *smem) {
+    const int N = I.n[2 - d];
+    int lg = 0;
+    while ((1 << lg) < N) ++lg;
+    const float2 *tw = a.tw[lg - 1];
+    if (d == 0) {
+        switch (N) {
+            case 32: rag_contig<32, S>(I, tile, tw, a.ci, I.scale[0], smem); break;
+            case 64: rag_contig<64, S>(I, tile, tw, a.ci, I.scale[0], smem); break;
+            case 128: rag_contig<128, S>(I, tile, tw, a.ci, I.scale[0], smem); break;
+            default: rag_contig<256, S>(I, tile, tw, a.ci, I.scale[0], smem); break;
+        }
+    } else {
+        const float sx = I.scale[d], sy = d == 2 ? a.co * I.scale[d] : I.scale[d];
+        switch (N) {
+            case 32: rag_strided<32, S>(I, d, tile, tw, sx, sy, smem); break;
+            case 64: rag_strided<64, S>(I, d, tile, tw, sx, sy, smem); break;
+            case 128: rag_strided<128, S>(I, d, tile, tw, sx, sy, smem); break;
+            default: rag_strided<256, S>(I, d, tile, tw, sx, sy, smem); break;
+        }
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(RAG_THREADS) ragged_kernel(RagArgs a) {
+    __shared__ float2 smem[rag_smem_elems()];
+    __shared__ int4 s_item;
+    __shared__ RagInst s_inst;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            const int ticket = (int)atomicAdd(&a.ctr[0], 1u);
+            int4 it = make_int4(ITEM_END, 0, 0, 0);
+            if (ticket < a.nitems) {
+                const RagItem e = a.items[ticket];
+                it = make_int4(e.flags, e.inst, e.tile, 0);
+            }
+            if (it.x & ITEM_WAIT) {
+                const int d = (it.x >> 8) & 3;  // wait for superstep d-1 of this instance
+                const RagInst &I = a.inst[it.y];
+                const uint32_t *dep = a.ctr + 1 + 2 * it.y + (d - 1);
+                const uint32_t target = (uint32_t)I.tiles[d - 1];
+                if (ld_acquire_u32(dep) < target) {
+                    const uint64_t dl = gtimer() + a.timeout_ns;
+                    while (ld_acquire_u32(dep) < target) {
+                        if (gtimer() > dl) {
+                            atomicExch(a.status, 1);
+                            it.x = ITEM_SKIP;
+                            break;
+                        }
+                        __nanosleep(100);
+                    }
+                }
+                __threadfence();
+            }
+            s_item = it;
+            if (!(it.x & (ITEM_END | ITEM_SKIP))) s_inst = a.inst[it.y];
+        }
+        __syncthreads();
+        const int4 it = s_item;
+        if (it.x & ITEM_END) break;
+        if (!(it.x & ITEM_SKIP)) {
+            const RagInst I = s_inst;
+            rag_tile<S>(a, I, (it.x >> 8) & 3, it.z, smem);
+        }
+        __syncthreads();
+        if ((it.x & ITEM_SIGNAL) && !(it.x & ITEM_SKIP) && tid == 0) {
+            __threadfence();
+            red_release_add_u32(a.ctr + 1 + 2 * it.y + ((it.x >> 8) & 3), 1u);
+        }
+    }
+}
+
+}  // namespace wsfft

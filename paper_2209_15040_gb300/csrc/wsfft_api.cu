@@ -33,6 +33,8 @@
 #include "engine.cuh"
 #include "engine_desc.h"
 #include "plan_internal.h"
+#include "ragged.cuh"
+#include "ragged_desc.h"
 
 using namespace wsfft;
 
@@ -502,6 +504,10 @@ void Plan::prof_end(cudaStream_t st) {
 
 Plan::~Plan() {
     for (auto e : prof_ev) cudaEventDestroy(e);
+    if (rag_items) cudaFree(rag_items);
+    if (rag_inst) cudaFree(rag_inst);
+    if (rag_inst_host) cudaFreeHost(rag_inst_host);
+    if (rag_copied) cudaEventDestroy(rag_copied);
     if (d_items) cudaFree(d_items);
     if (d_ctr) cudaFree(d_ctr);
     for (auto &kv : tables) cudaFree(kv.second);
@@ -581,20 +587,21 @@ int wsfft_plan_create(wsfft_plan *plan, const int64_t *dims, int rank, int dtype
 int wsfft_plan_set_norm(wsfft_plan plan, int norm) {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || norm < WSFFT_NORM_PAPER || norm > WSFFT_NORM_FORWARD) return WSFFT_ERR_INVALID_ARG;
+    if (p->ragged) return WSFFT_ERR_UNSUPPORTED;
     p->norm = norm;
     return p->build_schedule();
 }
 
 int wsfft_execute(wsfft_plan plan, const void *in, void *out, wsfft_stream stream) {
     Plan *p = reinterpret_cast<Plan *>(plan);
-    if (!p || !in || !out) return WSFFT_ERR_INVALID_ARG;
+    if (!p || p->ragged || !in || !out) return WSFFT_ERR_INVALID_ARG;
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return WSFFT_ERR_INVALID_ARG;
     return p->run(in, out, (cudaStream_t)stream);
 }
 
 int wsfft_execute_host(wsfft_plan plan, const void *host_in, void *host_out, wsfft_stream stream) {
     Plan *p = reinterpret_cast<Plan *>(plan);
-    if (!p || !host_in || !host_out) return WSFFT_ERR_INVALID_ARG;
+    if (!p || p->ragged || !host_in || !host_out) return WSFFT_ERR_INVALID_ARG;
     const size_t bytes = (size_t)(p->batch * p->elems * elem_bytes(p->dtype));
     if (!p->host_buf) {
         if (cudaMalloc(&p->host_buf, bytes) != cudaSuccess) {
@@ -681,8 +688,9 @@ int wsfft_plan_sync_status(wsfft_plan plan, wsfft_stream stream) {
 int wsfft_plan_passes(wsfft_plan plan, int *passes, int64_t *bytes) {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p) return WSFFT_ERR_INVALID_ARG;
-    if (passes) *passes = (int)p->passes.size();
-    if (bytes) *bytes = (int64_t)p->passes.size() * 2 * p->batch * p->elems * elem_bytes(p->dtype);
+    const int np = p->ragged ? 3 : (int)p->passes.size();
+    if (passes) *passes = np;
+    if (bytes) *bytes = (int64_t)np * 2 * p->batch * p->elems * elem_bytes(p->dtype);
     return WSFFT_SUCCESS;
 }
 
@@ -718,15 +726,149 @@ int wsfft_plan_launch_times(wsfft_plan plan, float *ms, int capacity, int *count
 
 int wsfft_plan_create_ragged(wsfft_plan *plan, int count, const int64_t *dims, int dtype,
                              int direction) {
-    if (plan) *plan = nullptr;
-    (void)count; (void)dims; (void)dtype; (void)direction;
-    return WSFFT_ERR_UNSUPPORTED;
+    if (!plan) return WSFFT_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (!dims || count < 1 || count > (1 << 20)) return WSFFT_ERR_INVALID_ARG;
+    if (dtype != WSFFT_C32 && dtype != WSFFT_C16F && dtype != WSFFT_C16BF) return WSFFT_ERR_INVALID_ARG;
+    if (direction != WSFFT_FORWARD && direction != WSFFT_INVERSE) return WSFFT_ERR_INVALID_ARG;
+    for (int i = 0; i < 3 * count; ++i)
+        if (!is_pow2(dims[i]) || dims[i] < 32 || dims[i] > 256) return WSFFT_ERR_INVALID_SIZE;
+    Plan *p = new (std::nothrow) Plan();
+    if (!p) return WSFFT_ERR_ALLOC;
+    p->ragged = true;
+    p->rag_count = count;
+    p->dtype = dtype;
+    p->dir = direction;
+    p->norm = dtype == WSFFT_C32 ? WSFFT_NORM_PAPER : WSFFT_NORM_ORTHO;
+    p->batch = 1;
+    auto fail = [&](int rc) {
+        delete p;
+        return rc;
+    };
+    if (cudaGetDevice(&p->device) != cudaSuccess) return fail(WSFFT_ERR_CUDA);
+    cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    if (cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) {
+        p->d_status = nullptr;
+        return fail(WSFFT_ERR_ALLOC);
+    }
+    cudaMemset(p->d_status, 0, sizeof(int));
+    const bool inv = direction == WSFFT_INVERSE;
+    std::vector<RagInst> inst((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        RagInst &I = inst[i];
+        memset(&I, 0, sizeof(I));
+        for (int d = 0; d < 3; ++d) I.n[d] = (int)dims[3 * i + d];
+        I.log_n2 = ilog2(I.n[2]);
+        I.log_n12 = ilog2((int64_t)I.n[1] * I.n[2]);
+        const int64_t n0 = I.n[0], n1 = I.n[1], n2 = I.n[2];
+        I.tiles[0] = (int)((n0 * n1 + rag_P((int)n2) - 1) / rag_P((int)n2));
+        I.tiles[1] = (int)((n0 * n2 + rag_W((int)n1) - 1) / rag_W((int)n1));
+        I.tiles[2] = (int)((n1 * n2 + rag_W((int)n0) - 1) / rag_W((int)n0));
+        // scales of the z, y, x supersteps
+        I.scale[0] = axis_scale(n2, direction, p->norm);
+        I.scale[1] = axis_scale(n1, direction, p->norm);
+        I.scale[2] = axis_scale(n0, direction, p->norm);
+        for (int d = 0; d < 3; ++d) {
+            const int N = I.n[d];
+            const float2 *t = p->table(N, rag_E(N));
+            if (!t) return fail(WSFFT_ERR_ALLOC);
+            p->rag_tw[ilog2(N) - 1] = t;
+        }
+    }
+    p->elems = 0;
+    for (auto &I : inst) p->elems += (int64_t)I.n[0] * I.n[1] * I.n[2];
+    // queue: z tiles of instance s, y tiles of s-1, x tiles of s-2
+    std::vector<RagItem> items;
+    for (int s = 0; s < count + 2; ++s) {
+        if (s < count)
+            for (int t = 0; t < inst[s].tiles[0]; ++t) items.push_back(RagItem{ITEM_SIGNAL | (0 << 8), s, t, 0});
+        if (s - 1 >= 0 && s - 1 < count)
+            for (int t = 0; t < inst[s - 1].tiles[1]; ++t)
+                items.push_back(RagItem{ITEM_STRIDED | ITEM_WAIT | ITEM_SIGNAL | (1 << 8), s - 1, t, 0});
+        if (s - 2 >= 0)
+            for (int t = 0; t < inst[s - 2].tiles[2]; ++t)
+                items.push_back(RagItem{ITEM_STRIDED | ITEM_WAIT | (2 << 8), s - 2, t, 0});
+    }
+    if (items.size() > (size_t)0x7fffffff) return fail(WSFFT_ERR_UNSUPPORTED);
+    p->rag_nitems = (int)items.size();
+    const size_t ib = items.size() * sizeof(RagItem), nb = inst.size() * sizeof(RagInst);
+    if (cudaMalloc(&p->rag_items, ib) != cudaSuccess) {
+        p->rag_items = nullptr;
+        return fail(WSFFT_ERR_ALLOC);
+    }
+    if (cudaMalloc(&p->rag_inst, nb) != cudaSuccess) {
+        p->rag_inst = nullptr;
+        return fail(WSFFT_ERR_ALLOC);
+    }
+    if (cudaMallocHost(&p->rag_inst_host, nb) != cudaSuccess) {
+        p->rag_inst_host = nullptr;
+        return fail(WSFFT_ERR_ALLOC);
+    }
+    memcpy(p->rag_inst_host, inst.data(), nb);
+    if (cudaMemcpy(p->rag_items, items.data(), ib, cudaMemcpyHostToDevice) != cudaSuccess) return fail(WSFFT_ERR_CUDA);
+    if (cudaMalloc(&p->d_ctr, (size_t)(1 + 2 * count) * sizeof(uint32_t)) != cudaSuccess) {
+        p->d_ctr = nullptr;
+        return fail(WSFFT_ERR_ALLOC);
+    }
+    p->ctr_cap = 1 + 2 * count;
+    if (cudaEventCreateWithFlags(&p->rag_copied, cudaEventDisableTiming) != cudaSuccess) {
+        p->rag_copied = nullptr;
+        return fail(WSFFT_ERR_CUDA);
+    }
+    int per_sm = 0;
+    RagArgs dummy{};
+    cudaError_t e = dtype == WSFFT_C32 ? launch_ragged_c32(dummy, &per_sm, 0, 0)
+                    : dtype == WSFFT_C16F ? launch_ragged_c16f(dummy, &per_sm, 0, 0)
+                                          : launch_ragged_c16bf(dummy, &per_sm, 0, 0);
+    if (e != cudaSuccess || per_sm < 1) return fail(WSFFT_ERR_CUDA);
+    p->rag_grid = per_sm * p->sm_count;
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(WSFFT_ERR_CUDA);
+    *plan = reinterpret_cast<wsfft_plan>(p);
+    return WSFFT_SUCCESS;
 }
 
 int wsfft_execute_ragged(wsfft_plan plan, const void *const *in, void *const *out,
                          wsfft_stream stream) {
-    (void)plan; (void)in; (void)out; (void)stream;
-    return WSFFT_ERR_UNSUPPORTED;
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !p->ragged || !in || !out) return WSFFT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    RagInst *h = static_cast<RagInst *>(p->rag_inst_host);
+    bool changed = !p->rag_uploaded;
+    for (int i = 0; i < p->rag_count; ++i) {
+        if (!in[i] || !out[i] || ((uintptr_t)in[i] & 15) || ((uintptr_t)out[i] & 15)) return WSFFT_ERR_INVALID_ARG;
+        changed |= h[i].in != in[i] || h[i].out != out[i];
+    }
+    if (changed) {
+        // the previous upload may still be reading the pinned table
+        if (p->rag_uploaded && cudaEventSynchronize(p->rag_copied) != cudaSuccess) return WSFFT_ERR_CUDA;
+        for (int i = 0; i < p->rag_count; ++i) {
+            h[i].in = in[i];
+            h[i].out = out[i];
+        }
+        if (cudaMemcpyAsync(p->rag_inst, h, sizeof(RagInst) * (size_t)p->rag_count, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+            return WSFFT_ERR_CUDA;
+        if (cudaEventRecord(p->rag_copied, st) != cudaSuccess) return WSFFT_ERR_CUDA;
+        p->rag_uploaded = true;
+    }
+    if (cudaMemsetAsync(p->d_ctr, 0, sizeof(uint32_t) * (size_t)(1 + 2 * p->rag_count), st) != cudaSuccess)
+        return WSFFT_ERR_CUDA;
+    RagArgs a{};
+    a.items = static_cast<const RagItem *>(p->rag_items);
+    a.nitems = p->rag_nitems;
+    a.inst = static_cast<const RagInst *>(p->rag_inst);
+    a.ctr = p->d_ctr;
+    a.status = p->d_status;
+    for (int i = 0; i < 9; ++i) a.tw[i] = p->rag_tw[i];
+    a.ci = p->dir == WSFFT_INVERSE ? -1.f : 1.f;
+    a.co = a.ci;
+    a.timeout_ns = (uint64_t)p->wait_timeout_ns;
+    p->prof_begin(st);
+    cudaError_t e = p->dtype == WSFFT_C32 ? launch_ragged_c32(a, nullptr, p->rag_grid, st)
+                    : p->dtype == WSFFT_C16F ? launch_ragged_c16f(a, nullptr, p->rag_grid, st)
+                                             : launch_ragged_c16bf(a, nullptr, p->rag_grid, st);
+    p->prof_end(st);
+    return e == cudaSuccess ? WSFFT_SUCCESS : WSFFT_ERR_CUDA;
 }
 
 int wsfft_autotune(wsfft_plan plan, wsfft_stream stream) {

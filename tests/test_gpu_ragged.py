@@ -1,0 +1,112 @@
+"""GPU parity of the ragged batch: uneven 3D shapes in one persistent launch
+(the ragged configuration: 256 shapes with axes drawn from {32, 64, 128, 256}
+by seed 4), against the FP64 oracle and against one plan per instance, plus
+replay under a captured CUDA graph."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_15040_gb300 import build, inputs
+from paper_2209_15040_gb300 import wsfft as W
+from tests._helpers import DT, TOL, to_device, to_host_c128
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build_library()
+    W.lib()
+
+
+def make_inputs(shapes, dtype, seed0):
+    xs = [inputs.complex_input(tuple(s), seed0 + i, "normal", dtype) for i, s in enumerate(shapes)]
+    return xs, [to_device(x, dtype) for x in xs]
+
+
+@pytest.mark.parametrize("dtype", ["c32", "c16f", "c16bf"])
+@pytest.mark.parametrize("direction", [W.FORWARD, W.INVERSE])
+def test_small_ragged_vs_oracle(dtype, direction):
+    rng = np.random.default_rng(7)
+    shapes = rng.choice([32, 64, 128], size=(12, 3))
+    xs, xd = make_inputs(shapes, dtype, 100)
+    outs = [torch.empty_like(x) for x in xd]
+    plan = W.RaggedPlan(shapes, DT[dtype], direction)
+    plan.execute([x.data_ptr() for x in xd], [y.data_ptr() for y in outs])
+    torch.cuda.synchronize()
+    assert plan.sync_status() == W.SUCCESS
+    norm = oracle.NORM_PAPER if dtype == "c32" else oracle.NORM_ORTHO
+    for x, y in zip(xs, outs):
+        ref = oracle.fftn(inputs.storage_to_c128(x, dtype), sign=direction, norm=norm)
+        assert oracle.rel_l2(to_host_c128(y, dtype), ref) < TOL[dtype]
+    plan.close()
+
+
+def test_ragged_in_place():
+    shapes = np.array([[64, 32, 128], [32, 256, 32], [128, 64, 64]])
+    xs, xd = make_inputs(shapes, "c32", 200)
+    plan = W.RaggedPlan(shapes, W.C32, W.FORWARD)
+    plan.execute([x.data_ptr() for x in xd], [x.data_ptr() for x in xd])
+    torch.cuda.synchronize()
+    for x, y in zip(xs, xd):
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.fftn(x.astype(np.complex128))) < TOL["c32"]
+    plan.close()
+
+
+def test_ragged_256_shapes_seed4():
+    # the full ragged configuration; data generated on the device (seeded per
+    # instance), every instance checked against its own plan, every 8th
+    # against the FP64 oracle
+    shapes = inputs.ragged_shapes(256, 4)
+    g = torch.Generator(device="cuda")
+    xd, outs = [], []
+    for i, s in enumerate(shapes):
+        g.manual_seed(1000 + i)
+        xd.append(torch.view_as_complex(torch.randn(tuple(int(v) for v in s) + (2,), generator=g,
+                                                    device="cuda")).contiguous())
+        outs.append(torch.empty_like(xd[-1]))
+    plan = W.RaggedPlan(shapes, W.C32, W.FORWARD)
+    plan.execute([x.data_ptr() for x in xd], [y.data_ptr() for y in outs])
+    torch.cuda.synchronize()
+    assert plan.sync_status() == W.SUCCESS
+    worst = 0.0
+    for i, (s, x, y) in enumerate(zip(shapes, xd, outs)):
+        p1 = W.Plan(tuple(int(v) for v in s), W.C32, W.FORWARD, 1)
+        r = torch.empty_like(x)
+        p1.execute(x.data_ptr(), r.data_ptr())
+        torch.cuda.synchronize()
+        worst = max(worst, oracle.rel_l2(y.cpu().numpy(), r.cpu().numpy()))
+        p1.close()
+        if i % 8 == 0:
+            ref = oracle.fftn(x.cpu().numpy().astype(np.complex128))
+            assert oracle.rel_l2(y.cpu().numpy(), ref) < TOL["c32"], i
+    print(f"ragged 256 vs per-instance plans: worst rel_l2 {worst:.2e}")
+    assert worst < TOL["c32"]
+    plan.close()
+
+
+def test_ragged_under_cuda_graph():
+    shapes = inputs.ragged_shapes(16, 4)
+    xs, xd = make_inputs(shapes, "c32", 300)
+    outs = [torch.empty_like(x) for x in xd]
+    plan = W.RaggedPlan(shapes, W.C32, W.FORWARD)
+    ins, ous = [x.data_ptr() for x in xd], [y.data_ptr() for y in outs]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.execute(ins, ous, s)  # first call uploads the pointer table
+    torch.cuda.synchronize()
+    for y in outs:
+        y.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        plan.execute(ins, ous, torch.cuda.current_stream())
+    for _ in range(2):
+        for y in outs:
+            y.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        for x, y in zip(xs, outs):
+            assert oracle.rel_l2(y.cpu().numpy(), oracle.fftn(x.astype(np.complex128))) < TOL["c32"]
+    assert plan.sync_status() == W.SUCCESS
+    plan.close()
