@@ -245,6 +245,23 @@ def ragged_leg(W, dev, stream, reps=5):
             "hbm_gbs_3pass_equiv": round(3 * 2 * elems * 8 / (t_graph * 1e-6) / 1e9, 1)}
 
 
+def run_case(args):
+    """A small case for ncu captures: the default plan of one shape, a few
+    executes, nothing timed."""
+    from paper_2209_15040_gb300 import build as _build
+    from paper_2209_15040_gb300 import wsfft as W
+    _build.build_library()
+    dims = tuple(int(v) for v in args.case.split(","))
+    x = torch.view_as_complex(torch.randn(dims + (2,), device="cuda")).contiguous()
+    y = torch.empty_like(x)
+    plan = W.Plan(dims, W.C32, W.FORWARD, 1)
+    for _ in range(args.case_reps):
+        plan.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    print(json.dumps({"case": list(dims), "passes": plan.passes()[0], "reps": args.case_reps}))
+    plan.close()
+
+
 def timed_pairs(fwd, inv, x, y, steps, warmup, world, stream):
     for _ in range(warmup):
         fwd.execute(x.data_ptr(), y.data_ptr(), stream)
@@ -274,6 +291,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch leg")
+    ap.add_argument("--case", default=None,
+                    help="profiling helper: run the default plan of shape D0,D1,D2 "
+                         "--case-reps times (complex64 forward, N(0,1) input) and exit")
+    ap.add_argument("--case-reps", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.steps < 1:
@@ -282,6 +303,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.case:
+        run_case(args)
         return
 
     from paper_2209_15040_gb300 import build as _build

@@ -154,13 +154,12 @@ __global__ void __launch_bounds__(PCfg<NC, EC, P, NS, ES, W, float2>::THREADS, 2
             if (it.x & ITEM_STRIDED) {
                 const int w = tid % W, t = tid / W;
                 const int64_t base = (int64_t)it.y * a.unit_elems + (int64_t)it.z * W + w;
-                StridedAcc<float2, false, OP_CG, OP_CS> acc;
+                StridedAcc<float2, false, OP_CG, OP_CS, W> acc;
                 acc.in = reinterpret_cast<const float2 *>(a.s_src) + base;
                 acc.out = reinterpret_cast<float2 *>(a.s_dst) + base;
                 acc.sm = na_smem;
                 acc.stride = a.s_stride;
                 acc.w = w;
-                acc.W = W;
                 acc.ci = a.s_ci;
                 acc.epi = Epi{a.s_sx, a.s_sy};
                 acc.active = true;

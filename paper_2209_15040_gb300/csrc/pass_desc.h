@@ -17,6 +17,7 @@ struct PassArgs {
     int64_t trans_rows; // contiguous transposed store: rows per transform
     float tw_inv;       // four-step twiddle: 2 / L
     int tw_mask;        // four-step twiddle: L - 1
+    int64_t tile0;      // strided launches: index of the first tile (set by the launcher)
 };
 
 enum PassKind {

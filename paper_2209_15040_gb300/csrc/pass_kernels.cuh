@@ -53,7 +53,9 @@ struct Epi {
     float sx, sy;  // multiply re by sx, im by sy (sy = -sx conjugates)
 };
 
-template <class S, int LOP = OP_DEF, int SOP = OP_DEF>
+// PLAIN: no conjugation on load and no scaling on store (the forward pass
+// of the unscaled transform), which saves three multiplies per element.
+template <class S, int LOP = OP_DEF, int SOP = OP_DEF, bool PLAIN = false>
 struct ContigAcc {
     const S *in;   // this pencil's first element
     S *out;        // this pencil's first element (unused when transposing)
@@ -63,14 +65,18 @@ struct ContigAcc {
     bool active;
     __device__ __forceinline__ float2 gload(int k) const {
         float2 v = active ? Cvt<S>::template load<LOP>(in + k) : make_float2(0.f, 0.f);
-        v.y *= ci;
+        if constexpr (!PLAIN) v.y *= ci;
         return v;
     }
     __device__ __forceinline__ void gstore(int k, float2 v) const {
-        if (active) Cvt<S>::template store<SOP>(out + k, make_float2(v.x * epi.sx, v.y * epi.sy));
+        if constexpr (!PLAIN) v = make_float2(v.x * epi.sx, v.y * epi.sy);
+        if (active) Cvt<S>::template store<SOP>(out + k, v);
     }
-    __device__ __forceinline__ void sstore(int k, float2 v) const { sm[k + (k >> 4)] = v; }
-    __device__ __forceinline__ float2 sload(int k) const { return sm[k + (k >> 4)]; }
+    // element k sits at k + k/16: one pad per 16 spreads the radix-16/8
+    // Stockham patterns over all banks; unsigned keeps (t + 16m) >> 4 linear
+    __device__ __forceinline__ static int sidx(int k) { return (int)((unsigned)k + ((unsigned)k >> 4)); }
+    __device__ __forceinline__ void sstore(int k, float2 v) const { sm[sidx(k)] = v; }
+    __device__ __forceinline__ float2 sload(int k) const { return sm[sidx(k)]; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
     __device__ __forceinline__ void after_load() const {}
 };
@@ -86,7 +92,7 @@ struct ContigTransAcc : ContigAcc<S> {
     __device__ __forceinline__ void gstore(int k, float2 v) const { stage[k * (P + 1) + p] = v; }
 };
 
-template <int N, int E, int P, class S, bool TRANS>
+template <int N, int E, int P, class S, bool TRANS, bool PLAIN = false>
 __global__ void __launch_bounds__(P *(N / E))
     contig_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
     extern __shared__ float2 smem[];
@@ -97,8 +103,8 @@ __global__ void __launch_bounds__(P *(N / E))
     const int64_t q = tile * P + p;
     const bool active = q < a.npencils;
     if constexpr (!TRANS) {
-        ContigAcc<S> acc{in + q * N, out + q * N, smem + p * contig_PS(N), a.conj_in, {a.sx, a.sy},
-                         active};
+        ContigAcc<S, OP_DEF, OP_DEF, PLAIN> acc{in + q * N, out + q * N, smem + p * contig_PS(N), a.conj_in,
+                                                {a.sx, a.sy}, active};
         pencil_fft<N, E>(acc, t, a.tw);
     } else {
         ContigTransAcc<S> acc;
@@ -130,13 +136,13 @@ __global__ void __launch_bounds__(P *(N / E))
     }
 }
 
-template <class S, bool TWID, int LOP = OP_DEF, int SOP = OP_DEF>
+template <class S, bool TWID, int LOP, int SOP, int W, bool PLAIN = false>
 struct StridedAcc {
     const S *in;   // this pencil's first element
     S *out;
     float2 *sm;    // tile base in shared memory
     int64_t stride;
-    int w, W;
+    int w;
     float ci;
     Epi epi;
     bool active;
@@ -145,7 +151,7 @@ struct StridedAcc {
     int tw_mask;    // four-step: length - 1
     __device__ __forceinline__ float2 gload(int k) const {
         float2 v = active ? Cvt<S>::template load<LOP>(in + (int64_t)k * stride) : make_float2(0.f, 0.f);
-        v.y *= ci;
+        if constexpr (!PLAIN) v.y *= ci;
         return v;
     }
     __device__ __forceinline__ void gstore(int k, float2 v) const {
@@ -156,37 +162,43 @@ struct StridedAcc {
             sincospif((float)m * tw_inv, &s, &c);
             v = cmul(v, make_float2(c, -s));
         }
-        if (active)
-            Cvt<S>::template store<SOP>(out + (int64_t)k * stride, make_float2(v.x * epi.sx, v.y * epi.sy));
+        if constexpr (!PLAIN) v = make_float2(v.x * epi.sx, v.y * epi.sy);
+        if (active) Cvt<S>::template store<SOP>(out + (int64_t)k * stride, v);
     }
-    __device__ __forceinline__ int sidx(int k) const { return k * W + w + ((k * W) >> 4); }
+    // row k of W elements plus one pad per 16 elements; linear in k when W is
+    // a multiple of 16, so every index is a per-thread base plus a constant
+    __device__ __forceinline__ int sidx(int k) const {
+        if constexpr (W % 16 == 0) return k * (W + W / 16) + w;
+        else return k * W + w + ((k * W) >> 4);
+    }
     __device__ __forceinline__ void sstore(int k, float2 v) const { sm[sidx(k)] = v; }
     __device__ __forceinline__ float2 sload(int k) const { return sm[sidx(k)]; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
     __device__ __forceinline__ void after_load() const {}
 };
 
-template <int N, int E, int W, class S, bool TWID>
-__global__ void __launch_bounds__(W *(N / E))
+// Blocks of up to 512 threads are held to 1024 threads per SM worth of
+// registers (two 512-thread blocks at 64 registers): measured faster at
+// 512^3 than letting the compiler use more registers and fit one block.
+template <int N, int E, int W, class S, bool TWID, bool PLAIN = false>
+__global__ void __launch_bounds__(W *(N / E), (W * (N / E) <= 512) ? 1024 / (W * (N / E)) : 1)
     strided_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
     extern __shared__ float2 smem[];
     const int w = threadIdx.x % W;
     const int t = threadIdx.x / W;
-    const int64_t q = (int64_t)blockIdx.x * W + w;
-    const bool active = q < a.npencils;
+    const int64_t q = ((int64_t)blockIdx.x + a.tile0) * W + w;
     const int64_t o = q >> a.log_inner;
     const int64_t i = q & (a.inner - 1);
     const int64_t base = o * ((int64_t)N << a.log_inner) + i;
-    StridedAcc<S, TWID> acc;
+    StridedAcc<S, TWID, OP_DEF, OP_DEF, W, PLAIN> acc;
     acc.in = in + base;
     acc.out = out + base;
     acc.sm = smem;
     acc.stride = a.inner;
     acc.w = w;
-    acc.W = W;
     acc.ci = a.conj_in;
     acc.epi = {a.sx, a.sy};
-    acc.active = active;
+    acc.active = q < a.npencils;
     acc.twq = (int)i;
     acc.tw_inv = a.tw_inv;
     acc.tw_mask = a.tw_mask;

@@ -15,13 +15,18 @@ cudaError_t set_smem(K kernel, int bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+inline bool plain_pass(const PassArgs &a) { return a.conj_in == 1.f && a.sx == 1.f && a.sy == 1.f; }
+
 template <int N, int E, int P, class S, bool TRANS>
 cudaError_t launch_contig(const void *in, void *out, const PassArgs &a, cudaStream_t st) {
     constexpr int T = N / E;
     constexpr int smem = contig_smem_elems(N, E, P, TRANS) * (int)sizeof(float2);
-    auto kern = contig_kernel<N, E, P, S, TRANS>;
-    static cudaError_t attr = set_smem(kern, smem);
-    if (attr != cudaSuccess) return attr;
+    const bool plain = !TRANS && plain_pass(a);
+    auto kern = plain ? contig_kernel<N, E, P, S, TRANS, !TRANS> : contig_kernel<N, E, P, S, TRANS, false>;
+    static cudaError_t attr0 = set_smem(contig_kernel<N, E, P, S, TRANS, false>, smem);
+    static cudaError_t attr1 = set_smem(contig_kernel<N, E, P, S, TRANS, !TRANS>, smem);
+    if (attr0 != cudaSuccess) return attr0;
+    if (attr1 != cudaSuccess) return attr1;
     const int64_t blocks = (a.npencils + P - 1) / P;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -33,13 +38,23 @@ template <int N, int E, int W, class S, bool TWID>
 cudaError_t launch_strided(const void *in, void *out, const PassArgs &a, cudaStream_t st) {
     constexpr int T = N / E;
     constexpr int smem = strided_smem_elems(N, E, W) * (int)sizeof(float2);
-    auto kern = strided_kernel<N, E, W, S, TWID>;
-    static cudaError_t attr = set_smem(kern, smem);
+    constexpr bool P1 = !TWID;  // a plain variant exists only without the four-step twiddle
+    const bool plain = !TWID && plain_pass(a);
+    static cudaError_t attr = [] {
+        cudaError_t e = set_smem(strided_kernel<N, E, W, S, TWID, false>, smem);
+        if (e == cudaSuccess) e = set_smem(strided_kernel<N, E, W, S, TWID, P1>, smem);
+        return e;
+    }();
     if (attr != cudaSuccess) return attr;
     const int64_t blocks = (a.npencils + W - 1) / W;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)blocks, W * T, smem, st>>>((const S *)in, (S *)out, a);
+    PassArgs b = a;
+    b.tile0 = 0;
+    if (plain)
+        strided_kernel<N, E, W, S, TWID, P1><<<(unsigned)blocks, W * T, smem, st>>>((const S *)in, (S *)out, b);
+    else
+        strided_kernel<N, E, W, S, TWID, false><<<(unsigned)blocks, W * T, smem, st>>>((const S *)in, (S *)out, b);
     return cudaGetLastError();
 }
 

@@ -97,25 +97,23 @@ __global__ void __launch_bounds__(PCfg<NC, EC, P, NS, ES, W, S>::THREADS, 2)
             const int64_t base = (int64_t)it.y * a.unit_elems + (int64_t)it.z * W + w;
             const Epi epi{a.s_sx, a.s_sy};
             if constexpr (MODE == 0) {
-                StridedAcc<S, false, OP_CG, OP_CS> acc;
+                StridedAcc<S, false, OP_CG, OP_CS, W> acc;
                 acc.in = reinterpret_cast<const S *>(a.s_src) + base;
                 acc.out = reinterpret_cast<S *>(a.s_dst) + base;
                 acc.sm = p_smem;
                 acc.stride = a.s_stride;
                 acc.w = w;
-                acc.W = W;
                 acc.ci = a.s_ci;
                 acc.epi = epi;
                 acc.active = true;
                 pencil_fft<NS, ES>(acc, t, a.tw_s);
             } else {
-                StridedAcc<S, false, OP_CS, OP_CS> acc;
+                StridedAcc<S, false, OP_CS, OP_CS, W> acc;
                 acc.in = reinterpret_cast<const S *>(a.s_src) + base;
                 acc.out = reinterpret_cast<S *>(a.s_dst) + base;
                 acc.sm = p_smem;
                 acc.stride = a.s_stride;
                 acc.w = w;
-                acc.W = W;
                 acc.ci = a.s_ci;
                 acc.epi = epi;
                 acc.active = true;

@@ -85,4 +85,8 @@ struct Plan {
     ~Plan();
 };
 
+// Apply a choice remembered by wsfft_autotune for this plan's key (no
+// timing); true if one was applied.
+bool autotune_apply_cached(Plan &p);
+
 }  // namespace wsfft

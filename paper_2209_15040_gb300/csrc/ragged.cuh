@@ -92,13 +92,12 @@ __device__ __forceinline__ void rag_strided(const RagInst &I, int d, int tile, c
     const int64_t q = (int64_t)tile * W + w;
     const int64_t o = q >> log_inner, i = q & (inner - 1);
     const int64_t base = o * ((int64_t)N << log_inner) + i;
-    StridedAcc<S, false, OP_CG, OP_DEF> acc;
+    StridedAcc<S, false, OP_CG, OP_DEF, W> acc;
     acc.in = reinterpret_cast<const S *>(I.out) + base;
     acc.out = reinterpret_cast<S *>(I.out) + base;
     acc.sm = smem;
     acc.stride = inner;
     acc.w = w;
-    acc.W = W;
     acc.ci = 1.f;
     acc.epi = Epi{sx, sy};
     acc.active = q < npen;

@@ -373,6 +373,17 @@ int Plan::build_schedule() {
             p.transform_elems = total;
             passes.push_back(p);
         }
+        if (dtype == WSFFT_C32 && norm != WSFFT_NORM_ORTHO) {
+            // complex64 has the range to defer every superstep's 1/n to the
+            // last pass (one scaled store instead of one per pass); the
+            // reduced-precision types keep the per-superstep scale
+            double total_scale = 1.0;
+            for (auto &p : passes) {
+                total_scale *= p.scale;
+                p.scale = 1.f;
+            }
+            passes.back().scale = (float)total_scale;
+        }
     }
     for (auto &kv : overrides) {
         if (kv.first < (int)passes.size() && !passes[kv.first].variant &&
@@ -576,6 +587,7 @@ int wsfft_plan_create(wsfft_plan *plan, const int64_t *dims, int rank, int dtype
         delete p;
         return rc;
     }
+    autotune_apply_cached(*p);  // a remembered choice for this key, if any
     if (cudaDeviceSynchronize() != cudaSuccess) {
         delete p;
         return WSFFT_ERR_CUDA;
@@ -871,9 +883,5 @@ int wsfft_execute_ragged(wsfft_plan plan, const void *const *in, void *const *ou
     return e == cudaSuccess ? WSFFT_SUCCESS : WSFFT_ERR_CUDA;
 }
 
-int wsfft_autotune(wsfft_plan plan, wsfft_stream stream) {
-    (void)stream;
-    return plan ? WSFFT_SUCCESS : WSFFT_ERR_INVALID_ARG;
-}
 
 }  // extern "C"

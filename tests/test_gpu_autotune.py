@@ -1,0 +1,66 @@
+"""GPU checks of wsfft_autotune: it picks a schedule and kernel shapes by
+timing them, the result stays a correct transform, and the choice is
+remembered in the WSFFT_TUNE_CACHE file and reused by later plans."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_15040_gb300 import build, inputs
+from paper_2209_15040_gb300 import wsfft as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build_library()
+    W.lib()
+
+
+def test_autotune_cube_and_cache(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("WSFFT_TUNE_CACHE", str(cache))
+    n = 128
+    xs = inputs.complex_input((n, n, n), 1, "normal", "c32")
+    x = torch.from_numpy(xs).cuda()
+    y = torch.empty_like(x)
+    plan = W.Plan((n, n, n), W.C32, W.FORWARD, 1)
+    plan.autotune()
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 1
+    entry = json.loads(lines[0])
+    assert entry["mode"] in (0, 1, 2, 3) and entry["us"] > 0
+    plan.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    ref = oracle.fftn(xs.astype(np.complex128))
+    assert oracle.rel_l2(y.cpu().numpy(), ref) < 5e-6
+    npass = plan.passes()[0]
+    plan.close()
+    # a new plan for the same key takes the remembered schedule without timing
+    plan2 = W.Plan((n, n, n), W.C32, W.FORWARD, 1)
+    assert plan2.passes()[0] == npass
+    plan2.autotune()
+    assert len(cache.read_text().strip().splitlines()) == 1
+    y.zero_()
+    plan2.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    assert oracle.rel_l2(y.cpu().numpy(), ref) < 5e-6
+    plan2.close()
+
+
+def test_autotune_2d_without_cache(monkeypatch):
+    monkeypatch.delenv("WSFFT_TUNE_CACHE", raising=False)
+    xs = inputs.complex_input((2, 512, 256), 3, "normal", "c32")
+    x = torch.from_numpy(xs).cuda()
+    y = torch.empty_like(x)
+    plan = W.Plan((512, 256), W.C32, W.INVERSE, 2)
+    plan.autotune()
+    plan.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    ref = oracle.fftn(xs.astype(np.complex128), rank=2, sign=+1)
+    assert oracle.rel_l2(y.cpu().numpy(), ref) < 5e-6
+    plan.close()
