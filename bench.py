@@ -40,6 +40,34 @@ PAPER_CS2_US = 959.3  # Table 1, 512^3 FP32 on a CS-2 (other hardware: context)
 REF_PASSES = 2        # minimum-bytes roofline: 2 passes over the array for 3D
 
 
+def source_sha256() -> str:
+    """Fingerprint of the CUDA sources, to tell whether recorded counters
+    still describe the kernels being run."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2209_15040_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(pass_index: int):
+    """DRAM bytes (read + write) of one launch of the given pass, from the
+    ncu capture recorded in profiles/traffic.json; None once the kernels
+    have changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    if rec.get("source_sha256") != source_sha256():
+        return None
+    return rec.get("c32_512_pass%d" % pass_index)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -357,11 +385,7 @@ def main():
     dom = int(np.argmax(mean_ms))
     bytes_launch = 2 * ELEMS * 8  # one read and one write of the array
     achieved = bytes_launch / (mean_ms[dom] * 1e-3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        with open(tr_path) as f:
-            traffic = json.load(f).get("c32_512_pass%d" % dom)
+    traffic = kernel_traffic(dom)
 
     # --- FP16 / BF16 storage, same step
     half = {}
