@@ -124,7 +124,7 @@ class Clocks:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.ident, f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -273,6 +273,42 @@ def ragged_leg(W, dev, stream, reps=5):
             "hbm_gbs_3pass_equiv": round(3 * 2 * elems * 8 / (t_graph * 1e-6) / 1e9, 1)}
 
 
+def run_sweep(args):
+    """Batched 1D transforms of length n (the analogue of the paper's
+    single-processor pencil experiment, Section 5.1) over 2^27 elements."""
+    from paper_2209_15040_gb300 import build as _build
+    from paper_2209_15040_gb300 import wsfft as W
+    _build.build_library()
+    hbm, kind = peaks()
+    total = 1 << 27
+    for dtype, code, tdt, eb in (("c32", W.C32, None, 8), ("c16f", W.C16F, torch.float16, 4)):
+        if tdt is None:
+            x = torch.view_as_complex(torch.randn(total, 2, device="cuda")).contiguous()
+        else:
+            x = torch.randn(total, 2, device="cuda", dtype=tdt)
+        y = torch.empty_like(x)
+        for lg in range(4, 13):
+            n = 1 << lg
+            plan = W.Plan((n,), code, W.FORWARD, total // n)
+            for _ in range(3):
+                plan.execute(x.data_ptr(), y.data_ptr())
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                plan.execute(x.data_ptr(), y.data_ptr())
+            e1.record()
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) / args.steps * 1e3
+            flops = 5.0 * n * lg * (total // n)
+            gbs = 2 * total * eb / (us * 1e-6) / 1e9
+            print(json.dumps({"sweep": "batched 1D", "n": n, "batch": total // n, "dtype": dtype,
+                              "us": round(us, 1), "gflops": round(flops / (us * 1e-6) / 1e9, 1),
+                              "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3),
+                              "peak_kind": kind}), flush=True)
+            plan.close()
+        del x, y
+
+
 def run_case(args):
     """A small case for ncu captures: the default plan of one shape, a few
     executes, nothing timed."""
@@ -313,7 +349,7 @@ def timed_pairs(fwd, inv, x, y, steps, warmup, world, stream):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wsfft", choices=["wsfft", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
@@ -323,6 +359,9 @@ def main():
                     help="profiling helper: run the default plan of shape D0,D1,D2 "
                          "--case-reps times (complex64 forward, N(0,1) input) and exit")
     ap.add_argument("--case-reps", type=int, default=3)
+    ap.add_argument("--sweep", action="store_true",
+                    help="batched 1D pencil sweep n = 16..4096 over 2^27 complex elements "
+                         "(FP32 and FP16 storage); one JSON line per point, then exit")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.steps < 1:
@@ -334,6 +373,9 @@ def main():
         return
     if args.case:
         run_case(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
 
     from paper_2209_15040_gb300 import build as _build

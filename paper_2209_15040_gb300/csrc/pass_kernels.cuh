@@ -41,7 +41,7 @@ __host__ __device__ constexpr int contig_PS(int N) { return N + N / 16 + 4; }
 
 __host__ __device__ constexpr int contig_smem_elems(int N, int E, int P, bool trans) {
     return (N / E) == 1 && !trans
-               ? 0
+               ? P * (N + 1)  // one thread per pencil: staging tile for coalesced copies
                : (P * contig_PS(N) > (trans ? N * (P + 1) : 0) ? P * contig_PS(N) : N * (P + 1));
 }
 __host__ __device__ constexpr int strided_smem_elems(int N, int E, int W) {
@@ -81,6 +81,27 @@ struct ContigAcc {
     __device__ __forceinline__ void after_load() const {}
 };
 
+// One thread's pencil staged in a shared-memory row (first loads and last
+// stores of the register FFT go to the row; no exchanges happen).
+template <class S, bool PLAIN>
+struct WarpStagedRow {
+    float2 *row;
+    float ci, sx, sy;
+    __device__ __forceinline__ float2 gload(int k) const {
+        float2 v = row[k];
+        if constexpr (!PLAIN) v.y *= ci;
+        return v;
+    }
+    __device__ __forceinline__ void gstore(int k, float2 v) const {
+        if constexpr (!PLAIN) v = make_float2(v.x * sx, v.y * sy);
+        row[k] = v;
+    }
+    __device__ __forceinline__ void sstore(int k, float2 v) const { row[k] = v; }
+    __device__ __forceinline__ float2 sload(int k) const { return row[k]; }
+    __device__ __forceinline__ void sync() const {}
+    __device__ __forceinline__ void after_load() const {}
+};
+
 // Contiguous axis, transposed store for the four-step split of a long 1D
 // axis: the result of pencil p (row k2 of transform b) element k goes to
 // out[b*N + k*rows + k2], staged through shared memory so the global store
@@ -102,7 +123,21 @@ __global__ void __launch_bounds__(P *(N / E))
     const int64_t tile = blockIdx.x;
     const int64_t q = tile * P + p;
     const bool active = q < a.npencils;
-    if constexpr (!TRANS) {
+    if constexpr (!TRANS && T == 1) {
+        // One thread per pencil (N <= 16): a thread's own loads would be N*8
+        // bytes apart across the warp, so the block copies its P*N-element
+        // slab (contiguous in memory) through shared memory, row stride N+1.
+        const int64_t base = tile * P * N;
+        const int64_t avail = (a.npencils - tile * P) * N;  // elements present in this tile
+        for (int e = threadIdx.x; e < P * N; e += P)
+            if (e < avail) smem[(e / N) * (N + 1) + e % N] = Cvt<S>::load(in + base + e);
+        __syncthreads();
+        WarpStagedRow<S, PLAIN> acc{smem + p * (N + 1), a.conj_in, a.sx, a.sy};
+        pencil_fft<N, E>(acc, t, a.tw);
+        __syncthreads();
+        for (int e = threadIdx.x; e < P * N; e += P)
+            if (e < avail) Cvt<S>::store(out + base + e, smem[(e / N) * (N + 1) + e % N]);
+    } else if constexpr (!TRANS) {
         ContigAcc<S, OP_DEF, OP_DEF, PLAIN> acc{in + q * N, out + q * N, smem + p * contig_PS(N), a.conj_in,
                                                 {a.sx, a.sy}, active};
         pencil_fft<N, E>(acc, t, a.tw);

@@ -139,3 +139,40 @@ def test_withheld_signal_times_out_and_plan_recovers(mode):
     assert plan.sync_status() == W.SUCCESS
     assert oracle.rel_l2(to_host_c128(y, "c32"), oracle.fftn(xc)) < TOL["c32"]
     plan.close()
+
+
+# -- 1024^3 (the paper's estimated point; 8 GiB complex64) -------------------------
+
+def test_1024cubed_forward_sampled():
+    # full-size 1024^3: coefficients by direct O(N) summation in the oracle,
+    # Parseval and the forward/inverse round trip on the device
+    n = 1024
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    x = torch.view_as_complex(torch.randn(n, n, n, 2, generator=g, device="cuda")).contiguous()
+    y = torch.empty_like(x)
+    fwd = W.Plan((n, n, n), W.C32, W.FORWARD, 1)
+    fwd.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    assert fwd.sync_status() == W.SUCCESS
+    N = float(n) ** 3
+    px = torch.linalg.vector_norm(torch.view_as_real(x).double()) ** 2
+    py = torch.linalg.vector_norm(torch.view_as_real(y).double()) ** 2
+    assert abs(float(py / (N * px)) - 1.0) < 1e-5
+    k = np.array([0, 1, 1025, 1 << 29, (1 << 30) - 1])
+    got = y.reshape(-1)[torch.from_numpy(k).cuda()].cpu().numpy().astype(np.complex128)
+    xs = x.cpu().numpy()
+    ref = oracle.dft_points(xs, k)
+    scale = np.sqrt(N)  # |X| ~ sqrt(N) for N(0,1) entries
+    err = np.max(np.abs(got - ref)) / scale
+    print(f"1024^3 sampled max err / sqrt(N): {err:.2e}")
+    assert err < 5e-5
+    del xs
+    inv = W.Plan((n, n, n), W.C32, W.INVERSE, 1)
+    inv.execute(y.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    rt = float(torch.linalg.vector_norm(y - x) / torch.linalg.vector_norm(x))
+    print(f"1024^3 round trip rel_l2 {rt:.2e}")
+    assert rt < 5e-6
+    fwd.close()
+    inv.close()
