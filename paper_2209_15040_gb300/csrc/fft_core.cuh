@@ -30,6 +30,19 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
+// A float4 carries the same element of two adjacent pencils,
+// (re0, im0, re1, im1); both halves get identical arithmetic and twiddles.
+__device__ __forceinline__ float4 cadd(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 csub(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ float4 cmul(float4 a, float2 b) {
+    return make_float4(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x), fmaf(a.z, b.x, -a.w * b.y),
+                       fmaf(a.z, b.y, a.w * b.x));
+}
+
 // a * exp(-2*pi*i*J/16) for a compile-time J.  The constants are cos and sin
 // of multiples of pi/8.
 template <int J>
@@ -65,29 +78,34 @@ __device__ __forceinline__ float2 rot16(float2 a) {
     }
 }
 
+template <int J>
+__device__ __forceinline__ float4 rot16(float4 a) {
+    const float2 lo = rot16<J>(make_float2(a.x, a.y)), hi = rot16<J>(make_float2(a.z, a.w));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 // In-register R-point forward DFT (R in {1,2,4,8,16}), natural order in and
 // out: split into even and odd halves, transform each, combine with
 // exp(-2*pi*i*k/R).
-template <int R, int K>
-__device__ __forceinline__ void dft_combine(float2 (&a)[R], const float2 (&e)[R / 2],
-                                            const float2 (&o)[R / 2]) {
+template <int R, int K, class V>
+__device__ __forceinline__ void dft_combine(V (&a)[R], const V (&e)[R / 2], const V (&o)[R / 2]) {
     if constexpr (K < R / 2) {
-        const float2 t = rot16<K * (16 / R)>(o[K]);
+        const V t = rot16<K * (16 / R)>(o[K]);
         a[K] = cadd(e[K], t);
         a[K + R / 2] = csub(e[K], t);
         dft_combine<R, K + 1>(a, e, o);
     }
 }
 
-template <int R>
-__device__ __forceinline__ void dft(float2 (&a)[R]) {
+template <int R, class V>
+__device__ __forceinline__ void dft(V (&a)[R]) {
     static_assert(R == 1 || R == 2 || R == 4 || R == 8 || R == 16, "radix");
     if constexpr (R == 2) {
-        const float2 t = a[0];
+        const V t = a[0];
         a[0] = cadd(t, a[1]);
         a[1] = csub(t, a[1]);
     } else if constexpr (R > 2) {
-        float2 e[R / 2], o[R / 2];
+        V e[R / 2], o[R / 2];
 #pragma unroll
         for (int i = 0; i < R / 2; ++i) {
             e[i] = a[2 * i];
@@ -148,9 +166,19 @@ struct Sched {
 //   sstore(k, v), sload(k)  -- shared-memory element k of the pencil
 //   sync()                  -- barrier over every thread that shares the tile
 //   after_load()            -- called once the first stage's inputs are in registers
-template <int N, int E, int S_IDX, class Acc>
-__device__ __forceinline__ void run_stages(float2 (&a)[E], Acc &acc, int t,
-                                           const float2 *__restrict__ tw) {
+// value type of an accessor: float2 (one pencil) unless it declares
+// `using value_type = float4` (a pencil pair)
+template <class Acc, class = void>
+struct AccValue {
+    using type = float2;
+};
+template <class Acc>
+struct AccValue<Acc, decltype((void)sizeof(typename Acc::value_type), void())> {
+    using type = typename Acc::value_type;
+};
+
+template <int N, int E, int S_IDX, class Acc, class V>
+__device__ __forceinline__ void run_stages(V (&a)[E], Acc &acc, int t, const float2 *__restrict__ tw) {
     using S = Sched<N, E>;
     constexpr int T = S::T;
     constexpr int NsPrev = S::ns_before(S_IDX - 1);
@@ -183,7 +211,7 @@ __device__ __forceinline__ void run_stages(float2 (&a)[E], Acc &acc, int t,
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const int k = (t + T * i) % Ns;
-            float2 g[R];
+            V g[R];
             g[0] = a[i * R];
 #pragma unroll
             for (int r = 1; r < R; ++r) g[r] = cmul(a[i * R + r], __ldg(&tw[TWO + (r - 1) * Ns + k]));
@@ -200,7 +228,7 @@ __device__ __forceinline__ void run_stages(float2 (&a)[E], Acc &acc, int t,
 template <int N, int E, class Acc>
 __device__ __forceinline__ void pencil_fft(Acc &acc, int t, const float2 *__restrict__ tw) {
     constexpr int T = Sched<N, E>::T;
-    float2 a[E];
+    typename AccValue<Acc>::type a[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) a[r] = acc.gload(t + r * T);
     acc.after_load();

@@ -20,6 +20,10 @@ struct PassArgs {
     int64_t tile0;      // strided launches: index of the first tile (set by the launcher)
 };
 
+// tile codes at or above this select the complex64 pencil-pair strided
+// kernel with (code - PAIR_TILE) pencils per block
+constexpr int PAIR_TILE = 1000;
+
 enum PassKind {
     PASS_CONTIG = 0,     // one launch, contiguous axis
     PASS_STRIDED = 1,    // one launch, strided axis

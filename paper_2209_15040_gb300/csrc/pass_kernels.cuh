@@ -240,4 +240,63 @@ __global__ void __launch_bounds__(W *(N / E), (W * (N / E) <= 512) ? 1024 / (W *
     pencil_fft<N, E>(acc, t, a.tw);
 }
 
+// Pencil pairs: thread (wp, t) carries pencils 2wp and 2wp+1 of a strided
+// tile as float4 values, so each global and shared access moves 16 bytes
+// (two adjacent elements of a row) and each twiddle serves both pencils.
+// Complex64 only; W pencils = W/2 pairs per row.
+template <int W, bool PLAIN>
+struct StridedPairAcc {
+    using value_type = float4;
+    const float4 *in;   // this pair's element 0
+    float4 *out;
+    float4 *sm;         // tile base, [k][W/2] float4
+    int64_t stride;     // in float4 units: element stride / 2
+    int wp;
+    float ci, sx, sy;
+    bool active;
+    __device__ __forceinline__ float4 gload(int k) const {
+        float4 v = active ? in[(int64_t)k * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (!PLAIN) {
+            v.y *= ci;
+            v.w *= ci;
+        }
+        return v;
+    }
+    __device__ __forceinline__ void gstore(int k, float4 v) const {
+        if constexpr (!PLAIN) v = make_float4(v.x * sx, v.y * sy, v.z * sx, v.w * sy);
+        if (active) out[(int64_t)k * stride] = v;
+    }
+    // a row of W/2 float4 is 8*W bytes; rows of 128 bytes cover all banks,
+    // so four rows per warp access are four wavefronts, the minimum
+    __device__ __forceinline__ int sidx(int k) const { return k * (W / 2) + wp; }
+    __device__ __forceinline__ void sstore(int k, float4 v) const { sm[sidx(k)] = v; }
+    __device__ __forceinline__ float4 sload(int k) const { return sm[sidx(k)]; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ void after_load() const {}
+};
+
+template <int N, int E, int W, bool PLAIN = false>
+__global__ void __launch_bounds__((W / 2) * (N / E), ((W / 2) * (N / E) <= 512) ? 1024 / ((W / 2) * (N / E)) : 1)
+    strided_pair_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, PassArgs a) {
+    extern __shared__ float4 psmem[];
+    constexpr int WP = W / 2;
+    const int wp = threadIdx.x % WP;
+    const int t = threadIdx.x / WP;
+    const int64_t q = ((int64_t)blockIdx.x + a.tile0) * W + 2 * wp;  // first pencil of the pair
+    const int64_t o = q >> a.log_inner;
+    const int64_t i = q & (a.inner - 1);
+    const int64_t base = o * ((int64_t)N << a.log_inner) + i;   // element offset (even)
+    StridedPairAcc<W, PLAIN> acc;
+    acc.in = reinterpret_cast<const float4 *>(in + base);
+    acc.out = reinterpret_cast<float4 *>(out + base);
+    acc.sm = psmem;
+    acc.stride = a.inner / 2;
+    acc.wp = wp;
+    acc.ci = a.conj_in;
+    acc.sx = a.sx;
+    acc.sy = a.sy;
+    acc.active = q < a.npencils;  // pencil counts are even multiples of W here
+    pencil_fft<N, E>(acc, t, a.tw);
+}
+
 }  // namespace wsfft
