@@ -241,21 +241,68 @@ __global__ void __launch_bounds__(W *(N / E), (W * (N / E) <= 512) ? 1024 / (W *
 }
 
 // Pencil pairs: thread (wp, t) carries pencils 2wp and 2wp+1 of a strided
-// tile as float4 values, so each global and shared access moves 16 bytes
-// (two adjacent elements of a row) and each twiddle serves both pencils.
-// Complex64 only; W pencils = W/2 pairs per row.
-template <int W, bool PLAIN>
+// tile as float4 values (re0, im0, re1, im1), so each global access moves
+// two adjacent elements of a row at once (16 bytes in complex64, 8 in the
+// half types), each shared access 16 bytes, and each twiddle serves both
+// pencils.  W pencils = W/2 pairs per row.
+template <class S>
+struct Pair;
+template <>
+struct Pair<float2> {
+    using T = float4;
+    __device__ __forceinline__ static float4 load(const T *p) { return *p; }
+    __device__ __forceinline__ static void store(T *p, float4 v) { *p = v; }
+};
+template <>
+struct Pair<__half2> {
+    using T = uint2;
+    __device__ __forceinline__ static float4 load(const T *p) {
+        const uint2 u = *p;
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    __device__ __forceinline__ static void store(T *p, float4 v) {
+        const __half2 a = __float22half2_rn(make_float2(v.x, v.y));
+        const __half2 b = __float22half2_rn(make_float2(v.z, v.w));
+        uint2 u;
+        u.x = *reinterpret_cast<const unsigned *>(&a);
+        u.y = *reinterpret_cast<const unsigned *>(&b);
+        *p = u;
+    }
+};
+template <>
+struct Pair<__nv_bfloat162> {
+    using T = uint2;
+    __device__ __forceinline__ static float4 load(const T *p) {
+        const uint2 u = *p;
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    __device__ __forceinline__ static void store(T *p, float4 v) {
+        const __nv_bfloat162 a = __float22bfloat162_rn(make_float2(v.x, v.y));
+        const __nv_bfloat162 b = __float22bfloat162_rn(make_float2(v.z, v.w));
+        uint2 u;
+        u.x = *reinterpret_cast<const unsigned *>(&a);
+        u.y = *reinterpret_cast<const unsigned *>(&b);
+        *p = u;
+    }
+};
+
+template <class S, int W, bool PLAIN>
 struct StridedPairAcc {
     using value_type = float4;
-    const float4 *in;   // this pair's element 0
-    float4 *out;
+    using PT = typename Pair<S>::T;
+    const PT *in;       // this pair's element 0
+    PT *out;
     float4 *sm;         // tile base, [k][W/2] float4
-    int64_t stride;     // in float4 units: element stride / 2
+    int64_t stride;     // in pair units: element stride / 2
     int wp;
     float ci, sx, sy;
     bool active;
     __device__ __forceinline__ float4 gload(int k) const {
-        float4 v = active ? in[(int64_t)k * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 v = active ? Pair<S>::load(in + (int64_t)k * stride) : make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (!PLAIN) {
             v.y *= ci;
             v.w *= ci;
@@ -264,7 +311,7 @@ struct StridedPairAcc {
     }
     __device__ __forceinline__ void gstore(int k, float4 v) const {
         if constexpr (!PLAIN) v = make_float4(v.x * sx, v.y * sy, v.z * sx, v.w * sy);
-        if (active) out[(int64_t)k * stride] = v;
+        if (active) Pair<S>::store(out + (int64_t)k * stride, v);
     }
     // a row of W/2 float4 is 8*W bytes; rows of 128 bytes cover all banks,
     // so four rows per warp access are four wavefronts, the minimum
@@ -275,10 +322,11 @@ struct StridedPairAcc {
     __device__ __forceinline__ void after_load() const {}
 };
 
-template <int N, int E, int W, bool PLAIN = false>
+template <int N, int E, int W, class S, bool PLAIN = false>
 __global__ void __launch_bounds__((W / 2) * (N / E), ((W / 2) * (N / E) <= 512) ? 1024 / ((W / 2) * (N / E)) : 1)
-    strided_pair_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, PassArgs a) {
+    strided_pair_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
     extern __shared__ float4 psmem[];
+    using PT = typename Pair<S>::T;
     constexpr int WP = W / 2;
     const int wp = threadIdx.x % WP;
     const int t = threadIdx.x / WP;
@@ -286,16 +334,16 @@ __global__ void __launch_bounds__((W / 2) * (N / E), ((W / 2) * (N / E) <= 512) 
     const int64_t o = q >> a.log_inner;
     const int64_t i = q & (a.inner - 1);
     const int64_t base = o * ((int64_t)N << a.log_inner) + i;   // element offset (even)
-    StridedPairAcc<W, PLAIN> acc;
-    acc.in = reinterpret_cast<const float4 *>(in + base);
-    acc.out = reinterpret_cast<float4 *>(out + base);
+    StridedPairAcc<S, W, PLAIN> acc;
+    acc.in = reinterpret_cast<const PT *>(in + base);
+    acc.out = reinterpret_cast<PT *>(out + base);
     acc.sm = psmem;
     acc.stride = a.inner / 2;
     acc.wp = wp;
     acc.ci = a.conj_in;
     acc.sx = a.sx;
     acc.sy = a.sy;
-    acc.active = q < a.npencils;  // pencil counts are even multiples of W here
+    acc.active = q < a.npencils;  // pencil counts are multiples of W here
     pencil_fft<N, E>(acc, t, a.tw);
 }
 

@@ -53,13 +53,13 @@ cudaError_t launch_strided(const void *in, void *out, const PassArgs &a, cudaStr
     return cudaGetLastError();
 }
 
-// Pencil-pair strided kernel (complex64): tile codes >= PAIR_TILE select it
-// with W = tile - PAIR_TILE pencils per block.
-template <int N, int E, int W>
+// Pencil-pair strided kernel: tile codes >= PAIR_TILE select it with
+// W = tile - PAIR_TILE pencils per block.
+template <int N, int E, int W, class S>
 cudaError_t launch_strided_pair(const void *in, void *out, const PassArgs &a, cudaStream_t st) {
     constexpr int TH = (W / 2) * (N / E);
     constexpr int smem = N * (W / 2) * (int)sizeof(float4);
-    static cudaError_t attr = set_smem(strided_pair_kernel<N, E, W, false>, smem);
+    static cudaError_t attr = set_smem(strided_pair_kernel<N, E, W, S, false>, smem);
     if (attr != cudaSuccess) return attr;
     if (a.npencils % W != 0 || a.inner % W != 0) return cudaErrorInvalidValue;
     const int64_t blocks = a.npencils / W;
@@ -70,7 +70,7 @@ cudaError_t launch_strided_pair(const void *in, void *out, const PassArgs &a, cu
     // The general variant (conjugate on load, scale on store) is used even
     // for plain passes: at 512^3 it measured 8% faster than the variant
     // without those multiplies.
-    strided_pair_kernel<N, E, W, false><<<(unsigned)blocks, TH, smem, st>>>((const float2 *)in, (float2 *)out, b);
+    strided_pair_kernel<N, E, W, S, false><<<(unsigned)blocks, TH, smem, st>>>((const S *)in, (S *)out, b);
     return cudaGetLastError();
 }
 
@@ -107,11 +107,9 @@ cudaError_t launch_extra(int kind, int N, int E, int tile, const void *in, void 
     WSFFT_XC(512, 16, 8)
     WSFFT_XC(512, 8, 8)
     WSFFT_XC(256, 8, 8)
-    if constexpr (std::is_same<S, float2>::value) {
-        if (kind == PASS_STRIDED && tile >= PAIR_TILE) {
-            if (N == 512 && E == 8 && tile == PAIR_TILE + 16) return launch_strided_pair<512, 8, 16>(in, out, a, st);
-            if (N == 256 && E == 8 && tile == PAIR_TILE + 16) return launch_strided_pair<256, 8, 16>(in, out, a, st);
-        }
+    if (kind == PASS_STRIDED && tile >= PAIR_TILE) {
+        if (N == 512 && E == 8 && tile == PAIR_TILE + 16) return launch_strided_pair<512, 8, 16, S>(in, out, a, st);
+        if (N == 256 && E == 8 && tile == PAIR_TILE + 16) return launch_strided_pair<256, 8, 16, S>(in, out, a, st);
     }
 #undef WSFFT_XC
 #undef WSFFT_XS

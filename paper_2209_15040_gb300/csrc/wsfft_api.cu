@@ -358,16 +358,10 @@ int Plan::build_schedule() {
             p.E = default_E(p.N);
             p.variant = false;
             if (p.kind == PASS_STRIDED && p.N == 512 && inner % 16 == 0) {
-                if (dtype == WSFFT_C32) {
-                    // measured fastest at 512^3: pencil pairs (16-byte accesses),
-                    // 8 values per pencil, 16 pencils of 128-byte rows per block
-                    p.E = 8;
-                    p.tile = PAIR_TILE + 16;
-                } else {
-                    // 16 values per thread, 16 pencils per 512-thread block
-                    p.E = 16;
-                    p.tile = 16;
-                }
+                // measured fastest at 512^3: pencil pairs (two adjacent elements
+                // per access), 8 values per pencil, 16 pencils per block
+                p.E = 8;
+                p.tile = PAIR_TILE + 16;
             }
             p.inner = inner;
             p.npencils_per_batch = total / d[ax];
