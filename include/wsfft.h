@@ -161,7 +161,8 @@ int wsfft_autotune(wsfft_plan plan, wsfft_stream stream);
  * UNSUPPORTED (that shape is not built for this pass). */
 int wsfft_plan_set_pass_variant(wsfft_plan plan, int pass, int values_per_thread, int tile);
 
-/* Choose the schedule of a rank-3 cube (n^3, n in {128, 256, 512, 1024}):
+/* Choose the schedule of a rank-3 transform n0 x n x n (n in {128, 256, 512,
+ * 1024}, any n0; the pipelined engine needs n0 == n):
  *   0 (default): one launch per superstep (three trips through HBM);
  *   3 (n <= 512): two trips through HBM with warp-per-pencil
  *      kernels -- a persistent kernel runs the supersteps along the two inner

@@ -22,10 +22,10 @@ cudaError_t launch_eng(const EngArgs &a, int grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int NC, int EC, int P, int NS, int ES, int W, class S, int MODE>
+template <int NC, int EC, int P, int NS, int ES, int W, class S, int MODE, bool PAIRS>
 cudaError_t launch_per_mode(const EngArgs &a, int *grid_per_sm, int grid, cudaStream_t st) {
-    using C = PCfg<NC, EC, P, NS, ES, W, S>;
-    auto kern = persist_kernel<NC, EC, P, NS, ES, W, S, MODE>;
+    using C = PCfg<NC, EC, P, NS, ES, W, S, PAIRS>;
+    auto kern = persist_kernel<NC, EC, P, NS, ES, W, S, MODE, PAIRS>;
     static cudaError_t attr =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (attr != cudaSuccess) return attr;
@@ -41,10 +41,10 @@ cudaError_t launch_per_mode(const EngArgs &a, int *grid_per_sm, int grid, cudaSt
     return cudaGetLastError();
 }
 
-template <int NC, int EC, int P, int NS, int ES, int W, class S>
+template <int NC, int EC, int P, int NS, int ES, int W, class S, bool PAIRS = false>
 cudaError_t launch_per(const EngArgs &a, int s_mode, int *grid_per_sm, int grid, cudaStream_t st) {
-    if (s_mode == 0) return launch_per_mode<NC, EC, P, NS, ES, W, S, 0>(a, grid_per_sm, grid, st);
-    return launch_per_mode<NC, EC, P, NS, ES, W, S, 1>(a, grid_per_sm, grid, st);
+    if (s_mode == 0) return launch_per_mode<NC, EC, P, NS, ES, W, S, 0, PAIRS>(a, grid_per_sm, grid, st);
+    return launch_per_mode<NC, EC, P, NS, ES, W, S, 1, PAIRS>(a, grid_per_sm, grid, st);
 }
 
 template <int N, class S>
@@ -112,7 +112,7 @@ cudaError_t WSFFT_PERSIST_NAME(int n, const EngArgs &a, int s_mode, int *grid_pe
     switch (n) {
         case 128: return launch_per<128, 16, 64, 128, 16, 64, S>(a, s_mode, grid_per_sm, grid, st);
         case 256: return launch_per<256, 16, 32, 256, 16, 32, S>(a, s_mode, grid_per_sm, grid, st);
-        case 512: return launch_per<512, 8, 8, 512, 8, 8, S>(a, s_mode, grid_per_sm, grid, st);
+        case 512: return launch_per<512, 8, 8, 512, 8, 16, S, true>(a, s_mode, grid_per_sm, grid, st);
         case 1024: return launch_per<1024, 16, 8, 1024, 16, 8, S>(a, s_mode, grid_per_sm, grid, st);
         default: return cudaErrorInvalidValue;
     }

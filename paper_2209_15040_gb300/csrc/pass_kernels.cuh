@@ -250,47 +250,53 @@ struct Pair;
 template <>
 struct Pair<float2> {
     using T = float4;
-    __device__ __forceinline__ static float4 load(const T *p) { return *p; }
-    __device__ __forceinline__ static void store(T *p, float4 v) { *p = v; }
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static float4 load(const T *p) { return ld_op<OP>(p); }
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static void store(T *p, float4 v) { st_op<OP>(p, v); }
 };
 template <>
 struct Pair<__half2> {
     using T = uint2;
+    template <int OP = OP_DEF>
     __device__ __forceinline__ static float4 load(const T *p) {
-        const uint2 u = *p;
+        const uint2 u = ld_op<OP>(p);
         const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
         const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
         return make_float4(a.x, a.y, b.x, b.y);
     }
+    template <int OP = OP_DEF>
     __device__ __forceinline__ static void store(T *p, float4 v) {
         const __half2 a = __float22half2_rn(make_float2(v.x, v.y));
         const __half2 b = __float22half2_rn(make_float2(v.z, v.w));
         uint2 u;
         u.x = *reinterpret_cast<const unsigned *>(&a);
         u.y = *reinterpret_cast<const unsigned *>(&b);
-        *p = u;
+        st_op<OP>(p, u);
     }
 };
 template <>
 struct Pair<__nv_bfloat162> {
     using T = uint2;
+    template <int OP = OP_DEF>
     __device__ __forceinline__ static float4 load(const T *p) {
-        const uint2 u = *p;
+        const uint2 u = ld_op<OP>(p);
         const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
         const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
         return make_float4(a.x, a.y, b.x, b.y);
     }
+    template <int OP = OP_DEF>
     __device__ __forceinline__ static void store(T *p, float4 v) {
         const __nv_bfloat162 a = __float22bfloat162_rn(make_float2(v.x, v.y));
         const __nv_bfloat162 b = __float22bfloat162_rn(make_float2(v.z, v.w));
         uint2 u;
         u.x = *reinterpret_cast<const unsigned *>(&a);
         u.y = *reinterpret_cast<const unsigned *>(&b);
-        *p = u;
+        st_op<OP>(p, u);
     }
 };
 
-template <class S, int W, bool PLAIN>
+template <class S, int W, bool PLAIN, int LOP = OP_DEF, int SOP = OP_DEF>
 struct StridedPairAcc {
     using value_type = float4;
     using PT = typename Pair<S>::T;
@@ -302,7 +308,7 @@ struct StridedPairAcc {
     float ci, sx, sy;
     bool active;
     __device__ __forceinline__ float4 gload(int k) const {
-        float4 v = active ? Pair<S>::load(in + (int64_t)k * stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 v = active ? Pair<S>::template load<LOP>(in + (int64_t)k * stride) : make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (!PLAIN) {
             v.y *= ci;
             v.w *= ci;
@@ -311,7 +317,7 @@ struct StridedPairAcc {
     }
     __device__ __forceinline__ void gstore(int k, float4 v) const {
         if constexpr (!PLAIN) v = make_float4(v.x * sx, v.y * sy, v.z * sx, v.w * sy);
-        if (active) Pair<S>::store(out + (int64_t)k * stride, v);
+        if (active) Pair<S>::template store<SOP>(out + (int64_t)k * stride, v);
     }
     // a row of W/2 float4 is 8*W bytes; rows of 128 bytes cover all banks,
     // so four rows per warp access are four wavefronts, the minimum

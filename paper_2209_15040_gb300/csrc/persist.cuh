@@ -19,12 +19,13 @@
 
 namespace wsfft {
 
-template <int NC, int EC, int P, int NS, int ES, int W, class S>
+// PAIRS: strided tiles carry pencil pairs (StridedPairAcc, W/2 pairs)
+template <int NC, int EC, int P, int NS, int ES, int W, class S, bool PAIRS = false>
 struct PCfg {
     static constexpr int THREADS = P * (NC / EC);
-    static_assert(THREADS == W * (NS / ES), "both tile kinds need the same thread count");
+    static_assert(THREADS == (PAIRS ? W / 2 : W) * (NS / ES), "both tile kinds need the same thread count");
     static constexpr int XC = P * contig_PS(NC);
-    static constexpr int XS = NS * W + (NS * W) / 16;
+    static constexpr int XS = PAIRS ? NS * W : NS * W + (NS * W) / 16;
     static constexpr int SMEM = (XC > XS ? XC : XS) * 8;
     static constexpr int TILE_C = P * NC;
 };
@@ -32,10 +33,10 @@ struct PCfg {
 // MODE 0 (pass A): contiguous and strided tiles; strided loads bypass L1
 // (.cg: the data was written by other blocks in this launch) and their stores
 // stream (.cs).  MODE 1 (pass B): strided tiles only, loads and stores stream.
-template <int NC, int EC, int P, int NS, int ES, int W, class S, int MODE>
-__global__ void __launch_bounds__(PCfg<NC, EC, P, NS, ES, W, S>::THREADS, 2)
+template <int NC, int EC, int P, int NS, int ES, int W, class S, int MODE, bool PAIRS = false>
+__global__ void __launch_bounds__(PCfg<NC, EC, P, NS, ES, W, S, PAIRS>::THREADS, 2)
     persist_kernel(EngArgs a) {
-    using C = PCfg<NC, EC, P, NS, ES, W, S>;
+    using C = PCfg<NC, EC, P, NS, ES, W, S, PAIRS>;
     extern __shared__ float2 p_smem[];
     __shared__ int4 s_item;
     const int tid = threadIdx.x;
@@ -93,6 +94,23 @@ __global__ void __launch_bounds__(PCfg<NC, EC, P, NS, ES, W, S>::THREADS, 2)
             continue;
         }
         if (it.x & ITEM_STRIDED) {
+          if constexpr (PAIRS) {
+            constexpr int WP = W / 2;
+            using PT = typename Pair<S>::T;
+            const int wp = tid % WP, t = tid / WP;
+            const int64_t base = (int64_t)it.y * a.unit_elems + (int64_t)it.z * W + 2 * wp;
+            StridedPairAcc<S, W, false, MODE == 0 ? OP_CG : OP_CS, OP_CS> acc;
+            acc.in = reinterpret_cast<const PT *>(reinterpret_cast<const S *>(a.s_src) + base);
+            acc.out = reinterpret_cast<PT *>(reinterpret_cast<S *>(a.s_dst) + base);
+            acc.sm = reinterpret_cast<float4 *>(p_smem);
+            acc.stride = a.s_stride / 2;
+            acc.wp = wp;
+            acc.ci = a.s_ci;
+            acc.sx = a.s_sx;
+            acc.sy = a.s_sy;
+            acc.active = true;
+            pencil_fft<NS, ES>(acc, t, a.tw_s);
+          } else {
             const int w = tid % W, t = tid / W;
             const int64_t base = (int64_t)it.y * a.unit_elems + (int64_t)it.z * W + w;
             const Epi epi{a.s_sx, a.s_sy};
@@ -119,6 +137,7 @@ __global__ void __launch_bounds__(PCfg<NC, EC, P, NS, ES, W, S>::THREADS, 2)
                 acc.active = true;
                 pencil_fft<NS, ES>(acc, t, a.tw_s);
             }
+          }
         } else if constexpr (MODE == 0) {
             constexpr int T = NC / EC;
             const int t = tid % T, p = tid / T;

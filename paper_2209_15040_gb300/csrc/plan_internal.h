@@ -77,7 +77,7 @@ struct Plan {
 
     const float2 *table(int N, int E);
     int build_schedule();
-    int build_engine(int64_t n, bool inv);
+    int build_engine(int64_t n0, int64_t n, bool inv);
     int run(const void *in, void *out, cudaStream_t st);
     // bracket one kernel launch with profiling events (no-op when off)
     void prof_begin(cudaStream_t st);

@@ -169,7 +169,7 @@ const float2 *Plan::table(int N, int E) {
 // strided superstep along the middle axis (y), queued `lag` slabs apart so
 // the slab is still in L2 when it is read again.  Pass B: the superstep along
 // the first axis (x).
-int Plan::build_engine(int64_t n, bool inv) {
+int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
     int grid = eng_grid;
     if (engine_mode == 1 || engine_mode == 3) {
         int per_sm = 0;
@@ -185,15 +185,18 @@ int Plan::build_engine(int64_t n, bool inv) {
     if (engine_mode == 3) {
         tp = wp_tile_z((int)n);
         tq = wp_tile_y((int)n);
+    } else if (engine_mode == 1 && n == 512) {
+        tp = 8;   // contiguous tiles: 8 pencils
+        tq = 16;  // strided tiles: 8 pencil pairs
     } else {
-        tp = (engine_mode == 1 && n == 512) ? 8 : engine_tile_pencils((int)n);
+        tp = engine_tile_pencils((int)n);
         tq = tp;
     }
     const int64_t zper = n / tp, yper = n / tq;       // tiles per slab of each kind
-    const int64_t U = batch * n;                      // slabs
+    const int64_t U = batch * n0;                     // slabs
     if (U * (zper + yper) > (int64_t)1 << 30) return WSFFT_ERR_UNSUPPORTED;
     const int64_t window = engine_mode == 2 ? 3 * (int64_t)grid : 2 * (int64_t)grid;  // tiles held
-    int64_t lag = (window + zper + yper - 1) / (zper + yper) + 2;
+    int64_t lag = (window + zper + yper - 1) / (zper + yper) + 2;  // measured: deeper lags do not help
     if (lag > U) lag = U;
     std::vector<EngItem> items;
     items.reserve((size_t)(U * (zper + yper) + batch * n * n / tq));
@@ -207,7 +210,7 @@ int Plan::build_engine(int64_t n, bool inv) {
     }
     if (withhold) items[0].flags &= ~ITEM_SIGNAL;
     const int na = (int)items.size();
-    if (engine_mode == 2)
+    if (engine_mode == 2)  // pipelined engine: x tiles too (cubes only, n0 == n)
         for (int64_t b = 0; b < batch; ++b)
             for (int64_t t = 0; t < n * n / tq; ++t) items.push_back(EngItem{ITEM_STRIDED, (int)b, (int)t, 0});
     const int nb = (int)items.size() - na;
@@ -230,7 +233,7 @@ int Plan::build_engine(int64_t n, bool inv) {
         }
         ctr_cap = 1 + U;
     }
-    const float sc = axis_scale(n, dir, norm);
+    const float sc = axis_scale(n, dir, norm), sc0 = axis_scale(n0, dir, norm);
     PassSpec a{};
     a.kind = engine_mode == 1 ? PASS_PERSIST_A : engine_mode == 3 ? PASS_WP_A : PASS_ENGINE_A;
     a.N = (int)n;
@@ -243,11 +246,11 @@ int Plan::build_engine(int64_t n, bool inv) {
     a.conj_in = inv;
     a.c_scale = sc;
     a.s_scale = sc;
-    a.transform_elems = n * n * n;
+    a.transform_elems = n0 * n * n;
     PassSpec b{};
-    if (engine_mode == 3) {
+    if (engine_mode == 3 && wp_supports((int)n0)) {
         b.kind = PASS_WP_B;
-        b.N = (int)n;
+        b.N = (int)n0;
         b.E = 16;
         b.inner = n * n;
         b.npencils_per_batch = n * n;
@@ -261,20 +264,20 @@ int Plan::build_engine(int64_t n, bool inv) {
         b.nitems = nb;
         b.units = 0;
     } else {
-        // x: one launch of the strided superstep kernel (512: 16 values per
-        // thread, 16 pencils of 128-byte rows per block)
+        // x: one launch of the strided superstep kernel (512: pencil pairs,
+        // 16 pencils of 128-byte rows per block)
         b.kind = PASS_STRIDED;
-        b.N = (int)n;
-        b.E = n == 512 ? 16 : default_E((int)n);
-        b.tile = n == 512 ? 16 : 0;
+        b.N = (int)n0;
+        b.E = n0 == 512 ? 8 : default_E((int)n0);
+        b.tile = n0 == 512 ? PAIR_TILE + 16 : 0;
         b.inner = n * n;
         b.npencils_per_batch = n * n;
         b.src = SRC_OUT;
         b.dst = DST_OUT;
     }
     b.conj_out = inv;
-    b.scale = sc;
-    b.transform_elems = n * n * n;
+    b.scale = engine_mode == 2 ? sc : sc0;
+    b.transform_elems = n0 * n * n;
     passes.push_back(a);
     passes.push_back(b);
     for (auto &kv : overrides) {
@@ -302,9 +305,12 @@ int Plan::build_schedule() {
     work_elems = 0;
     chunk = batch;
 
-    if (r == 3 && engine_mode != 0 && d[0] == d[1] && d[1] == d[2] && engine_supports((int)d[0]) &&
-        (engine_mode != 3 || wp_supports((int)d[0])) && eng_grid > 0) {
-        return build_engine(d[0], inv);
+    // fused schedules: the two inner axes equal (n x n slabs); the pipelined
+    // engine also runs the outer axis, so it needs a cube
+    if (r == 3 && engine_mode != 0 && d[1] == d[2] && engine_supports((int)d[1]) &&
+        (engine_mode != 2 || d[0] == d[1]) && (engine_mode != 3 || wp_supports((int)d[1])) &&
+        eng_grid > 0) {
+        return build_engine(d[0], d[1], inv);
     }
     if (r == 1 && d[0] > 4096) {
         const int64_t n = d[0];

@@ -176,3 +176,12 @@ def test_1024cubed_forward_sampled():
     assert rt < 5e-6
     fwd.close()
     inv.close()
+
+
+@pytest.mark.parametrize("mode", [1, 3])
+@pytest.mark.parametrize("shape", [(64, 512, 512), (32, 128, 128), (256, 256, 256), (2, 512, 512)])
+def test_fused_schedule_any_outer_axis(mode, shape):
+    xs, xc = seeded(shape, 12, "normal", "c32")
+    y, npass = run(to_device(xs, "c32"), shape, "c32", W.FORWARD, engine=mode)
+    assert npass == 2
+    assert oracle.rel_l2(to_host_c128(y, "c32"), oracle.fftn(xc)) < TOL["c32"]
