@@ -109,6 +109,8 @@ cudaError_t launch_extra(int kind, int N, int E, int tile, const void *in, void 
     WSFFT_XC(256, 8, 8)
     if (kind == PASS_STRIDED && tile >= PAIR_TILE) {
         if (N == 512 && E == 8 && tile == PAIR_TILE + 16) return launch_strided_pair<512, 8, 16, S>(in, out, a, st);
+        if (N == 512 && E == 8 && tile == PAIR_TILE + 32) return launch_strided_pair<512, 8, 32, S>(in, out, a, st);
+        if (N == 512 && E == 8 && tile == PAIR_TILE + 8) return launch_strided_pair<512, 8, 8, S>(in, out, a, st);
         if (N == 256 && E == 8 && tile == PAIR_TILE + 16) return launch_strided_pair<256, 8, 16, S>(in, out, a, st);
     }
 #undef WSFFT_XC

@@ -363,6 +363,12 @@ int Plan::build_schedule() {
             p.N = (int)d[ax];
             p.E = default_E(p.N);
             p.variant = false;
+            if (p.kind == PASS_CONTIG && p.N == 512) {
+                // measured fastest at 512^3: 16 values per thread (radices
+                // 16, 16, 2), 8 pencils per 256-thread block
+                p.E = 16;
+                p.tile = 8;
+            }
             if (p.kind == PASS_STRIDED && p.N == 512 && inner % 16 == 0) {
                 // measured fastest at 512^3: pencil pairs (two adjacent elements
                 // per access), 8 values per pencil, 16 pencils per block
