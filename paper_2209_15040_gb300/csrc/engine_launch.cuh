@@ -112,7 +112,7 @@ cudaError_t WSFFT_PERSIST_NAME(int n, const EngArgs &a, int s_mode, int *grid_pe
     switch (n) {
         case 128: return launch_per<128, 16, 64, 128, 16, 64, S>(a, s_mode, grid_per_sm, grid, st);
         case 256: return launch_per<256, 16, 32, 256, 16, 32, S>(a, s_mode, grid_per_sm, grid, st);
-        case 512: return launch_per<512, 8, 8, 512, 8, 16, S, true>(a, s_mode, grid_per_sm, grid, st);
+        case 512: return launch_per<512, 16, 16, 512, 8, 16, S, true>(a, s_mode, grid_per_sm, grid, st);
         case 1024: return launch_per<1024, 16, 8, 1024, 16, 8, S>(a, s_mode, grid_per_sm, grid, st);
         default: return cudaErrorInvalidValue;
     }

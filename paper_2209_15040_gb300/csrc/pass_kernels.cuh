@@ -55,7 +55,10 @@ struct Epi {
 
 // PLAIN: no conjugation on load and no scaling on store (the forward pass
 // of the unscaled transform), which saves three multiplies per element.
-template <class S, int LOP = OP_DEF, int SOP = OP_DEF, bool PLAIN = false>
+// WARP: the pencil's threads all sit in one warp (at most 32 threads per
+// pencil) and its exchange row is theirs alone, so the exchanges need only
+// a warp barrier.
+template <class S, int LOP = OP_DEF, int SOP = OP_DEF, bool PLAIN = false, bool WARP = false>
 struct ContigAcc {
     const S *in;   // this pencil's first element
     S *out;        // this pencil's first element (unused when transposing)
@@ -77,7 +80,10 @@ struct ContigAcc {
     __device__ __forceinline__ static int sidx(int k) { return (int)((unsigned)k + ((unsigned)k >> 4)); }
     __device__ __forceinline__ void sstore(int k, float2 v) const { sm[sidx(k)] = v; }
     __device__ __forceinline__ float2 sload(int k) const { return sm[sidx(k)]; }
-    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ void sync() const {
+        if constexpr (WARP) __syncwarp();
+        else __syncthreads();
+    }
     __device__ __forceinline__ void after_load() const {}
 };
 
@@ -138,8 +144,8 @@ __global__ void __launch_bounds__(P *(N / E))
         for (int e = threadIdx.x; e < P * N; e += P)
             if (e < avail) Cvt<S>::store(out + base + e, smem[(e / N) * (N + 1) + e % N]);
     } else if constexpr (!TRANS) {
-        ContigAcc<S, OP_DEF, OP_DEF, PLAIN> acc{in + q * N, out + q * N, smem + p * contig_PS(N), a.conj_in,
-                                                {a.sx, a.sy}, active};
+        ContigAcc<S, OP_DEF, OP_DEF, PLAIN, (T <= 32)> acc{in + q * N, out + q * N, smem + p * contig_PS(N),
+                                                           a.conj_in, {a.sx, a.sy}, active};
         pencil_fft<N, E>(acc, t, a.tw);
     } else {
         ContigTransAcc<S> acc;

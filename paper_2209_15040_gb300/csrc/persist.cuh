@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(PCfg<NC, EC, P, NS, ES, W, S, PAIRS>::THREADS,
             constexpr int T = NC / EC;
             const int t = tid % T, p = tid / T;
             const int64_t off = (int64_t)it.y * a.unit_elems + (int64_t)it.z * C::TILE_C + (int64_t)p * NC;
-            ContigAcc<S, OP_CS, OP_DEF> acc{reinterpret_cast<const S *>(a.c_src) + off,
+            ContigAcc<S, OP_CS, OP_DEF, false, (T <= 32)> acc{reinterpret_cast<const S *>(a.c_src) + off,
                                             reinterpret_cast<S *>(a.c_dst) + off,
                                             p_smem + p * contig_PS(NC),
                                             a.c_ci,

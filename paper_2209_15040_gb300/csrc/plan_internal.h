@@ -28,6 +28,7 @@ struct PassSpec {
     int64_t trans_rows;          // transposed store: rows per transform
     int64_t twid_len;            // four-step twiddle: length of the long axis
     const float2 *tw;            // device stage-twiddle table
+    const float2 *tw2;           // fused passes: table of the strided tiles, if it differs
     // persistent engine passes (kind PASS_ENGINE_A / PASS_ENGINE_B)
     const void *items;           // device item table
     int nitems;

@@ -186,7 +186,7 @@ int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
         tp = wp_tile_z((int)n);
         tq = wp_tile_y((int)n);
     } else if (engine_mode == 1 && n == 512) {
-        tp = 8;   // contiguous tiles: 8 pencils
+        tp = 16;  // contiguous tiles: 16 pencils, one warp each
         tq = 16;  // strided tiles: 8 pencil pairs
     } else {
         tp = engine_tile_pencils((int)n);
@@ -237,7 +237,7 @@ int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
     PassSpec a{};
     a.kind = engine_mode == 1 ? PASS_PERSIST_A : engine_mode == 3 ? PASS_WP_A : PASS_ENGINE_A;
     a.N = (int)n;
-    a.E = engine_mode == 1 && n == 512 ? 8 : 16;
+    a.E = 16;
     a.tile = (int)tp;
     a.trans_rows = zper;  // completion target of a slab
     a.items = d_items;
@@ -289,6 +289,11 @@ int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
     for (auto &p : passes) {
         p.tw = table(p.N, p.E);
         if (!p.tw) return WSFFT_ERR_ALLOC;
+    }
+    if (engine_mode == 1 && n == 512) {
+        // the persistent 512 kernel's strided tiles use 8 values per pencil
+        passes[0].tw2 = table(512, 8);
+        if (!passes[0].tw2) return WSFFT_ERR_ALLOC;
     }
     return WSFFT_SUCCESS;
 }
@@ -452,7 +457,7 @@ int Plan::run(const void *in, void *out, cudaStream_t st) {
                 e.ctr = d_ctr;
                 e.status = d_status;
                 e.tw_c = p.tw;
-                e.tw_s = p.tw;
+                e.tw_s = p.tw2 ? p.tw2 : p.tw;
                 e.timeout_ns = (uint64_t)wait_timeout_ns;
                 const int64_t n = p.N;
                 if (p.kind == PASS_ENGINE_A || p.kind == PASS_PERSIST_A || p.kind == PASS_WP_A) {
