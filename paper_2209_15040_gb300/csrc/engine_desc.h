@@ -12,6 +12,11 @@ struct EngArgs;
 // each has tiles of 8192 elements: P = W = 8192 / n pencils, 16 values per
 // thread, 512 consumer threads + one producer warp per block.
 inline bool engine_supports(int n) { return n == 128 || n == 256 || n == 512 || n == 1024; }
+// tiles per queue item of the persistent kernel (the 512 instantiation groups them)
+#ifndef WSFFT_PERSIST_SUB
+#define WSFFT_PERSIST_SUB 2
+#endif
+inline int persist_sub(int n) { return n == 512 ? WSFFT_PERSIST_SUB : 1; }
 inline int engine_tile_pencils(int n) { return 8192 / n; }
 
 // Persistent one-ticket-per-block kernel (persist.cuh).  grid_per_sm != NULL:

@@ -22,10 +22,13 @@ cudaError_t launch_eng(const EngArgs &a, int grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+#ifndef WSFFT_PERSIST_SUB
+#define WSFFT_PERSIST_SUB 2
+#endif
 template <int NC, int EC, int P, int NS, int ES, int W, class S, int MODE, bool PAIRS>
 cudaError_t launch_per_mode(const EngArgs &a, int *grid_per_sm, int grid, cudaStream_t st) {
     using C = PCfg<NC, EC, P, NS, ES, W, S, PAIRS>;
-    auto kern = persist_kernel<NC, EC, P, NS, ES, W, S, MODE, PAIRS>;
+    auto kern = persist_kernel<NC, EC, P, NS, ES, W, S, MODE, PAIRS, (PAIRS ? WSFFT_PERSIST_SUB : 1)>;
     static cudaError_t attr =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (attr != cudaSuccess) return attr;

@@ -33,7 +33,9 @@ struct PCfg {
 // MODE 0 (pass A): contiguous and strided tiles; strided loads bypass L1
 // (.cg: the data was written by other blocks in this launch) and their stores
 // stream (.cs).  MODE 1 (pass B): strided tiles only, loads and stores stream.
-template <int NC, int EC, int P, int NS, int ES, int W, class S, int MODE, bool PAIRS = false>
+// SUB: tiles per queue item (an item covers tiles tile*SUB .. tile*SUB+SUB-1),
+// which spreads the per-item ticket, dependency and barrier cost.
+template <int NC, int EC, int P, int NS, int ES, int W, class S, int MODE, bool PAIRS = false, int SUB = 1>
 __global__ void __launch_bounds__(PCfg<NC, EC, P, NS, ES, W, S, PAIRS>::THREADS, 2)
     persist_kernel(EngArgs a) {
     using C = PCfg<NC, EC, P, NS, ES, W, S, PAIRS>;
@@ -87,12 +89,17 @@ __global__ void __launch_bounds__(PCfg<NC, EC, P, NS, ES, W, S, PAIRS>::THREADS,
             s_item = it;
         }
         __syncthreads();
-        const int4 it = s_item;
-        if (it.x & ITEM_END) break;
-        if (it.x & ITEM_SKIP) {
+        const int4 it0 = s_item;
+        if (it0.x & ITEM_END) break;
+        if (it0.x & ITEM_SKIP) {
             __syncthreads();  // everyone has read s_item before thread 0 rewrites it
             continue;
         }
+#pragma unroll 1
+        for (int sub = 0; sub < SUB; ++sub) {
+        if (sub > 0) __syncthreads();  // the exchange buffer is reused by the next tile
+        int4 it = it0;
+        it.z = it0.z * SUB + sub;
         if (it.x & ITEM_STRIDED) {
           if constexpr (PAIRS) {
             constexpr int WP = W / 2;
@@ -150,10 +157,11 @@ __global__ void __launch_bounds__(PCfg<NC, EC, P, NS, ES, W, S, PAIRS>::THREADS,
                                             true};
             pencil_fft<NC, EC>(acc, t, a.tw_c);
         }
-        __syncthreads();  // tile done: exchange buffer and s_item free
-        if ((it.x & ITEM_SIGNAL) && tid == 0) {
+        }  // sub-tiles
+        __syncthreads();  // item done: exchange buffer and s_item free
+        if ((it0.x & ITEM_SIGNAL) && tid == 0) {
             __threadfence();
-            red_release_add_u32(a.ctr + 1 + it.y, 1u);
+            red_release_add_u32(a.ctr + 1 + it0.y, 1u);
         }
     }
 }

@@ -192,7 +192,8 @@ int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
         tp = engine_tile_pencils((int)n);
         tq = tp;
     }
-    const int64_t zper = n / tp, yper = n / tq;       // tiles per slab of each kind
+    const int64_t sub = engine_mode == 1 ? persist_sub((int)n) : 1;  // tiles per queue item
+    const int64_t zper = n / tp / sub, yper = n / tq / sub;  // queue items per slab of each kind
     const int64_t U = batch * n0;                     // slabs
     if (U * (zper + yper) > (int64_t)1 << 30) return WSFFT_ERR_UNSUPPORTED;
     const int64_t window = engine_mode == 2 ? 3 * (int64_t)grid : 2 * (int64_t)grid;  // tiles held
