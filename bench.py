@@ -494,7 +494,9 @@ def main():
             "metric": METRIC, "value": round(us_per_transform, 2), "unit": "us",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms_per_step, 4), "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": round(us_per_transform / PAPER_CS2_US, 4),
+            "vs_baseline_note": "value / 959.3 us, the paper's 512^3 FP32 time on a CS-2 (Table 1): context on other hardware",
+            "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dims": list(DIMS), "dtype": "complex64",
                        "input": "N(0,1) re/im, seeded, device-generated",
                        "l2": "inputs larger than L2 (1 GiB array vs 126 MB L2)",

@@ -73,7 +73,7 @@ __device__ __forceinline__ void rag_contig(const RagInst &I, int tile, const flo
     const int t = threadIdx.x % T, p = threadIdx.x / T;
     const int64_t npen = (int64_t)I.n[0] * I.n[1];
     const int64_t q = (int64_t)tile * P + p;
-    ContigAcc<S, OP_DEF, OP_DEF> acc{reinterpret_cast<const S *>(I.in) + q * N,
+    ContigAcc<S, OP_DEF, OP_DEF, false, (T <= 32)> acc{reinterpret_cast<const S *>(I.in) + q * N,
                                      reinterpret_cast<S *>(I.out) + q * N, smem + p * contig_PS(N), ci,
                                      {sc, sc}, q < npen};
     pencil_fft<N, rag_E(N)>(acc, t, tw);
