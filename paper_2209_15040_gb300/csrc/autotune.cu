@@ -128,10 +128,12 @@ double time_plan(Plan &p, const void *in, void *out, cudaStream_t st) {
 
 // (kind, N) -> extra shapes instantiated by pass_launch.cuh
 std::vector<std::pair<int, int>> shapes_for(int kind, int N) {
-    if (kind == PASS_STRIDED && N == 512) return {{16, 16}, {8, 8}, {16, 8}, {16, 32}, {8, PAIR_TILE + 16}, {8, PAIR_TILE + 32}, {8, PAIR_TILE + 8}};
+    if (kind == PASS_STRIDED && N == 512)
+        return {{32, 16}, {32, 8},  {32, 32}, {16, 16}, {8, 8}, {16, 8}, {16, 32}, {8, PAIR_TILE + 16},
+                {8, PAIR_TILE + 32}, {8, PAIR_TILE + 8}, {16, PAIR_TILE + 16}, {16, PAIR_TILE + 32}};
     if (kind == PASS_STRIDED && N == 256) return {{16, 32}, {8, 16}, {8, PAIR_TILE + 16}};
     if (kind == PASS_STRIDED && N == 1024) return {{16, 8}};
-    if (kind == PASS_CONTIG && N == 512) return {{16, 8}, {8, 8}};
+    if (kind == PASS_CONTIG && N == 512) return {{32, 16}, {32, 8}, {32, 32}, {16, 8}, {8, 8}};
     if (kind == PASS_CONTIG && N == 256) return {{8, 8}};
     return {};
 }

@@ -17,6 +17,15 @@ inline bool engine_supports(int n) { return n == 128 || n == 256 || n == 512 || 
 #define WSFFT_PERSIST_SUB 2
 #endif
 inline int persist_sub(int n) { return n == 512 ? WSFFT_PERSIST_SUB : 1; }
+// shape of the persistent 512 kernel's tiles: 1 = contiguous tiles of 8
+// pencils and strided tiles of 16 pencils with 32 values per thread; 0 =
+// contiguous tiles of 16 pencils and strided tiles of 8 pencil pairs with 8
+// values per pencil
+#ifndef WSFFT_PERSIST512_E32
+#define WSFFT_PERSIST512_E32 0
+#endif
+inline int persist512_tile_z() { return WSFFT_PERSIST512_E32 ? 8 : 16; }
+inline int persist512_values_y() { return WSFFT_PERSIST512_E32 ? 32 : 8; }
 inline int engine_tile_pencils(int n) { return 8192 / n; }
 
 // Persistent one-ticket-per-block kernel (persist.cuh).  grid_per_sm != NULL:

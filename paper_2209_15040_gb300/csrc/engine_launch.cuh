@@ -28,7 +28,7 @@ cudaError_t launch_eng(const EngArgs &a, int grid, cudaStream_t st) {
 template <int NC, int EC, int P, int NS, int ES, int W, class S, int MODE, bool PAIRS>
 cudaError_t launch_per_mode(const EngArgs &a, int *grid_per_sm, int grid, cudaStream_t st) {
     using C = PCfg<NC, EC, P, NS, ES, W, S, PAIRS>;
-    auto kern = persist_kernel<NC, EC, P, NS, ES, W, S, MODE, PAIRS, (PAIRS ? WSFFT_PERSIST_SUB : 1)>;
+    auto kern = persist_kernel<NC, EC, P, NS, ES, W, S, MODE, PAIRS, (NC == 512 ? WSFFT_PERSIST_SUB : 1)>;
     static cudaError_t attr =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (attr != cudaSuccess) return attr;
@@ -115,7 +115,11 @@ cudaError_t WSFFT_PERSIST_NAME(int n, const EngArgs &a, int s_mode, int *grid_pe
     switch (n) {
         case 128: return launch_per<128, 16, 64, 128, 16, 64, S>(a, s_mode, grid_per_sm, grid, st);
         case 256: return launch_per<256, 16, 32, 256, 16, 32, S>(a, s_mode, grid_per_sm, grid, st);
+#if WSFFT_PERSIST512_E32
+        case 512: return launch_per<512, 16, 8, 512, 32, 16, S>(a, s_mode, grid_per_sm, grid, st);
+#else
         case 512: return launch_per<512, 16, 16, 512, 8, 16, S, true>(a, s_mode, grid_per_sm, grid, st);
+#endif
         case 1024: return launch_per<1024, 16, 8, 1024, 16, 8, S>(a, s_mode, grid_per_sm, grid, st);
         default: return cudaErrorInvalidValue;
     }

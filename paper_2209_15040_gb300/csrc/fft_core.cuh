@@ -78,6 +78,41 @@ __device__ __forceinline__ float2 rot16(float2 a) {
     }
 }
 
+// cos(j*pi/16), j in [0, 32), from the first-octant values by symmetry
+__host__ __device__ constexpr double cos_pi16(int j) {
+    j = ((j % 32) + 32) % 32;
+    if (j > 16) j = 32 - j;              // cos(2pi - t) = cos t
+    if (j > 8) return -cos_pi16(16 - j);  // cos(pi - t) = -cos t
+    constexpr double base[9] = {1.0,
+                                0.98078528040323044912618223613424,   // cos(pi/16)
+                                0.92387953251128675612818318939679,   // cos(pi/8)
+                                0.83146961230254523707878837761791,   // cos(3pi/16)
+                                0.70710678118654752440084436210485,   // cos(pi/4)
+                                0.55557023301960222474283081394853,   // cos(5pi/16)
+                                0.38268343236508977172845998403040,   // cos(3pi/8)
+                                0.19509032201612826784828486847702,   // cos(7pi/16)
+                                0.0};
+    return base[j];
+}
+
+// a * exp(-2*pi*i*J/32) for a compile-time J: even J reuses rot16
+template <int J>
+__device__ __forceinline__ float2 rot32(float2 a) {
+    constexpr int j = ((J % 32) + 32) % 32;
+    if constexpr (j % 2 == 0) {
+        return rot16<j / 2>(a);
+    } else {
+        constexpr float c = (float)cos_pi16(j);
+        constexpr float s = (float)cos_pi16(8 - j);  // sin(j*pi/16)
+        return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+    }
+}
+template <int J>
+__device__ __forceinline__ float4 rot32(float4 a) {
+    const float2 lo = rot32<J>(make_float2(a.x, a.y)), hi = rot32<J>(make_float2(a.z, a.w));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 template <int J>
 __device__ __forceinline__ float4 rot16(float4 a) {
     const float2 lo = rot16<J>(make_float2(a.x, a.y)), hi = rot16<J>(make_float2(a.z, a.w));
@@ -90,7 +125,7 @@ __device__ __forceinline__ float4 rot16(float4 a) {
 template <int R, int K, class V>
 __device__ __forceinline__ void dft_combine(V (&a)[R], const V (&e)[R / 2], const V (&o)[R / 2]) {
     if constexpr (K < R / 2) {
-        const V t = rot16<K * (16 / R)>(o[K]);
+        const V t = rot32<K * (32 / R)>(o[K]);
         a[K] = cadd(e[K], t);
         a[K + R / 2] = csub(e[K], t);
         dft_combine<R, K + 1>(a, e, o);
@@ -99,7 +134,7 @@ __device__ __forceinline__ void dft_combine(V (&a)[R], const V (&e)[R / 2], cons
 
 template <int R, class V>
 __device__ __forceinline__ void dft(V (&a)[R]) {
-    static_assert(R == 1 || R == 2 || R == 4 || R == 8 || R == 16, "radix");
+    static_assert(R == 1 || R == 2 || R == 4 || R == 8 || R == 16 || R == 32, "radix");
     if constexpr (R == 2) {
         const V t = a[0];
         a[0] = cadd(t, a[1]);
@@ -150,7 +185,7 @@ __host__ __device__ constexpr int sched_tw_size(int N, int E) {
 
 template <int N, int E>
 struct Sched {
-    static_assert(E >= 1 && E <= 16 && (E & (E - 1)) == 0, "E");
+    static_assert(E >= 1 && E <= 32 && (E & (E - 1)) == 0, "E");
     static_assert(N >= E && (N & (N - 1)) == 0, "N");
     static constexpr int T = N / E;  // threads per pencil
     __host__ __device__ static constexpr int nstages() { return sched_nstages(N, E); }

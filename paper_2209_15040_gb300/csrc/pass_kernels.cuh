@@ -221,8 +221,14 @@ struct StridedAcc {
 // Blocks of up to 512 threads are held to 1024 threads per SM worth of
 // registers (two 512-thread blocks at 64 registers): measured faster at
 // 512^3 than letting the compiler use more registers and fit one block.
+// Blocks per SM the register budget is held to: 1024 threads per SM for up
+// to 16 values per thread, 512 threads per SM for 32 (their radix-32 stages
+// need about twice the registers).
+__host__ __device__ constexpr int strided_min_blocks(int threads, int values) {
+    return values >= 32 ? (threads <= 256 ? 512 / threads : 1) : (threads <= 512 ? 1024 / threads : 1);
+}
 template <int N, int E, int W, class S, bool TWID, bool PLAIN = false>
-__global__ void __launch_bounds__(W *(N / E), (W * (N / E) <= 512) ? 1024 / (W * (N / E)) : 1)
+__global__ void __launch_bounds__(W *(N / E), strided_min_blocks(W *(N / E), E))
     strided_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
     extern __shared__ float2 smem[];
     const int w = threadIdx.x % W;
@@ -335,7 +341,7 @@ struct StridedPairAcc {
 };
 
 template <int N, int E, int W, class S, bool PLAIN = false>
-__global__ void __launch_bounds__((W / 2) * (N / E), ((W / 2) * (N / E) <= 512) ? 1024 / ((W / 2) * (N / E)) : 1)
+__global__ void __launch_bounds__((W / 2) * (N / E), strided_min_blocks((W / 2) * (N / E), 2 * E))
     strided_pair_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
     extern __shared__ float4 psmem[];
     using PT = typename Pair<S>::T;

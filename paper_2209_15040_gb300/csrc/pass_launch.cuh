@@ -98,6 +98,9 @@ cudaError_t launch_extra(int kind, int N, int E, int tile, const void *in, void 
 #define WSFFT_XS(n, e, t) \
     if (kind == PASS_STRIDED && N == n && E == e && tile == t) return launch_strided<n, e, t, S, false>(in, out, a, st);
     WSFFT_XS(512, 16, 16)
+    WSFFT_XS(512, 32, 16)
+    WSFFT_XS(512, 32, 8)
+    WSFFT_XS(512, 32, 32)
     WSFFT_XS(512, 8, 8)
     WSFFT_XS(512, 16, 8)
     WSFFT_XS(512, 16, 32)
@@ -105,12 +108,17 @@ cudaError_t launch_extra(int kind, int N, int E, int tile, const void *in, void 
     WSFFT_XS(256, 8, 16)
     WSFFT_XS(1024, 16, 8)
     WSFFT_XC(512, 16, 8)
+    WSFFT_XC(512, 32, 16)
+    WSFFT_XC(512, 32, 8)
+    WSFFT_XC(512, 32, 32)
     WSFFT_XC(512, 8, 8)
     WSFFT_XC(256, 8, 8)
     if (kind == PASS_STRIDED && tile >= PAIR_TILE) {
         if (N == 512 && E == 8 && tile == PAIR_TILE + 16) return launch_strided_pair<512, 8, 16, S>(in, out, a, st);
         if (N == 512 && E == 8 && tile == PAIR_TILE + 32) return launch_strided_pair<512, 8, 32, S>(in, out, a, st);
         if (N == 512 && E == 8 && tile == PAIR_TILE + 8) return launch_strided_pair<512, 8, 8, S>(in, out, a, st);
+        if (N == 512 && E == 16 && tile == PAIR_TILE + 16) return launch_strided_pair<512, 16, 16, S>(in, out, a, st);
+        if (N == 512 && E == 16 && tile == PAIR_TILE + 32) return launch_strided_pair<512, 16, 32, S>(in, out, a, st);
         if (N == 256 && E == 8 && tile == PAIR_TILE + 16) return launch_strided_pair<256, 8, 16, S>(in, out, a, st);
     }
 #undef WSFFT_XC

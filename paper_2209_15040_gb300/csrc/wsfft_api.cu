@@ -186,8 +186,8 @@ int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
         tp = wp_tile_z((int)n);
         tq = wp_tile_y((int)n);
     } else if (engine_mode == 1 && n == 512) {
-        tp = 16;  // contiguous tiles: 16 pencils, one warp each
-        tq = 16;  // strided tiles: 8 pencil pairs
+        tp = persist512_tile_z();  // contiguous tiles: one warp per pencil
+        tq = 16;                   // strided tiles: 16 pencils
     } else {
         tp = engine_tile_pencils((int)n);
         tq = tp;
@@ -265,12 +265,13 @@ int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
         b.nitems = nb;
         b.units = 0;
     } else {
-        // x: one launch of the strided superstep kernel (512: pencil pairs,
-        // 16 pencils of 128-byte rows per block)
+        // x: one launch of the strided superstep kernel, with the shape of
+        // the one-launch-per-superstep schedule at 512 (16 pencils per block:
+        // 32 values per thread in complex64, pencil pairs in the 16-bit types)
         b.kind = PASS_STRIDED;
         b.N = (int)n0;
-        b.E = n0 == 512 ? 8 : default_E((int)n0);
-        b.tile = n0 == 512 ? PAIR_TILE + 16 : 0;
+        b.E = n0 == 512 ? (dtype == WSFFT_C32 ? 32 : 8) : default_E((int)n0);
+        b.tile = n0 == 512 ? (dtype == WSFFT_C32 ? 16 : PAIR_TILE + 16) : 0;
         b.inner = n * n;
         b.npencils_per_batch = n * n;
         b.src = SRC_OUT;
@@ -292,8 +293,8 @@ int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
         if (!p.tw) return WSFFT_ERR_ALLOC;
     }
     if (engine_mode == 1 && n == 512) {
-        // the persistent 512 kernel's strided tiles use 8 values per pencil
-        passes[0].tw2 = table(512, 8);
+        // the persistent 512 kernel's strided tiles have their own values per thread
+        passes[0].tw2 = table(512, persist512_values_y());
         if (!passes[0].tw2) return WSFFT_ERR_ALLOC;
     }
     return WSFFT_SUCCESS;
@@ -371,15 +372,19 @@ int Plan::build_schedule() {
             p.variant = false;
             if (p.kind == PASS_CONTIG && p.N == 512) {
                 // measured fastest at 512^3: 16 values per thread (radices
-                // 16, 16, 2), 8 pencils per 256-thread block
+                // 16, 16, 2), 8 pencils per 256-thread block (32 values per
+                // thread matched it forward but lost 30% with the conjugate
+                // on load of the inverse)
                 p.E = 16;
                 p.tile = 8;
             }
             if (p.kind == PASS_STRIDED && p.N == 512 && inner % 16 == 0) {
-                // measured fastest at 512^3: pencil pairs (two adjacent elements
-                // per access), 8 values per pencil, 16 pencils per block
-                p.E = 8;
-                p.tile = PAIR_TILE + 16;
+                // measured fastest at 512^3: complex64 with 32 values per
+                // thread and 16 pencils per block (one shared-memory exchange);
+                // the 16-bit types with pencil pairs (two adjacent elements per
+                // access), 8 values per pencil, 16 pencils per block
+                p.E = dtype == WSFFT_C32 ? 32 : 8;
+                p.tile = dtype == WSFFT_C32 ? 16 : PAIR_TILE + 16;
             }
             p.inner = inner;
             p.npencils_per_batch = total / d[ax];

@@ -1,0 +1,125 @@
+"""GPU parity of every kernel shape the library instantiates besides the
+defaults: each (values per thread, pencils per block) shape of the
+contiguous-axis and strided-axis superstep kernels, including the
+pencil-pair and the 32-values-per-thread (radix-32) shapes, selected with
+wsfft_plan_set_pass_variant and compared with the FP64 oracle, for every
+storage type, on full tiles and on ragged tails (pencil counts that are not a
+multiple of the tile)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_15040_gb300 import build
+from paper_2209_15040_gb300 import wsfft as W
+from tests._helpers import DT, TOL, seeded, to_device, to_host_c128
+
+pytestmark = pytest.mark.gpu
+
+PAIR = 1000  # tile codes from PAIR_TILE on select the pencil-pair kernel
+
+# (values per thread, tile) shapes per axis length
+CONTIG = {512: [(32, 16), (32, 8), (32, 32), (16, 8), (8, 8)], 256: [(8, 8)]}
+STRIDED = {512: [(32, 16), (32, 8), (32, 32), (16, 16), (8, 8), (16, 8), (16, 32)],
+           256: [(16, 32), (8, 16)], 1024: [(16, 8)]}
+PAIRS = {512: [(8, PAIR + 16), (8, PAIR + 32), (8, PAIR + 8), (16, PAIR + 16), (16, PAIR + 32)],
+         256: [(8, PAIR + 16)]}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build_library()
+    W.lib()
+    torch.cuda.init()
+
+
+_cache = {}
+
+
+def _case(shape_full, rank, dtype, seed):
+    key = (shape_full, rank, dtype, seed)
+    if key not in _cache:
+        xs, xc = seeded(shape_full, seed, "uniform", dtype)
+        norm = W.NORM_PAPER if dtype == "c32" else W.NORM_ORTHO
+        _cache[key] = (to_device(xs, dtype), oracle.fftn(xc, rank=rank, sign=W.FORWARD, norm=norm),
+                       norm)
+    return _cache[key]
+
+
+def run_variant(shape_full, rank, dtype, settings, seed=5):
+    x, ref, norm = _case(shape_full, rank, dtype, seed)
+    dims = shape_full[len(shape_full) - rank:]
+    batch = int(np.prod(shape_full[:len(shape_full) - rank], dtype=np.int64))
+    plan = W.Plan(dims, DT[dtype], W.FORWARD, batch, norm)
+    for pass_index, e, tile in settings:
+        plan.set_pass_variant(pass_index, e, tile)
+    out = torch.empty_like(x)
+    plan.execute(x.data_ptr(), out.data_ptr())
+    torch.cuda.synchronize()
+    assert plan.sync_status() == W.SUCCESS
+    plan.close()
+    y = to_host_c128(out, dtype)
+    err = oracle.rel_l2(y, ref)
+    print(f"{shape_full} {dtype} {settings}: rel_l2={err:.3e} max_abs={oracle.max_abs(y, ref):.3e}")
+    assert err < TOL[dtype], err
+
+
+DTYPES = ["c32", "c16f", "c16bf"]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape", CONTIG[512])
+def test_contig_512(dtype, shape):
+    # pass 0 is the contiguous superstep of length 512 (8*512 = 4096 pencils)
+    run_variant((64, 8, 512), 3, dtype, [(0, *shape)])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape", CONTIG[512])
+def test_contig_512_ragged(dtype, shape):
+    # 37 pencils: the last tile of every shape is partial
+    run_variant((37, 512), 1, dtype, [(0, *shape)])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape", STRIDED[512] + PAIRS[512])
+def test_strided_512(dtype, shape):
+    # pass 2 is the superstep along the outer axis (512, stride 8*64 elements)
+    # and pass 1 the one along the middle axis (8)
+    run_variant((512, 8, 64), 3, dtype, [(2, *shape)])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape", STRIDED[512])
+def test_strided_512_ragged(dtype, shape):
+    # batch 3 of 512 x 2: 6 strided pencils of 512, stride 2, in one partial tile
+    run_variant((3, 512, 2), 2, dtype, [(1, *shape)])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_pair_rejects_ragged(dtype):
+    # the pencil-pair kernel wants whole tiles: the plan accepts the shape
+    # (it exists) but the execute reports an error instead of running
+    x, _, norm = _case((3, 512, 2), 2, dtype, 5)
+    plan = W.Plan((512, 2), DT[dtype], W.FORWARD, 3, norm)
+    plan.set_pass_variant(1, 8, PAIR + 16)
+    out = torch.empty_like(x)
+    with pytest.raises(RuntimeError):
+        plan.execute(x.data_ptr(), out.data_ptr())
+    torch.cuda.synchronize()
+    plan.close()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_256_shapes(dtype):
+    for sh in CONTIG[256]:
+        run_variant((16, 8, 256), 3, dtype, [(0, *sh)])
+    for sh in STRIDED[256] + PAIRS[256]:
+        run_variant((256, 4, 32), 3, dtype, [(2, *sh)])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_1024_shapes(dtype):
+    for sh in STRIDED[1024]:
+        run_variant((1024, 4, 16), 3, dtype, [(2, *sh)])
+
