@@ -216,6 +216,51 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def sizes_leg(W, dev, stream, hbm_peak, steps=20, warmup=3):
+    """The other transform sizes of the workload family, each timed like the
+    main step ((FFT + IFFT)/2, data resident, CUDA events on the stream):
+    cubes 128^3, 256^3 and 1024^3 (complex64 and float16 storage), 2D
+    4096 x 4096 and 1D 2^20 x batch 512 (complex64).  GB/s counts one read and
+    one write of the array per launch; the minimum-bytes fraction uses 2
+    passes for 2D and 3D and 1 for 1D.  Arrays of 16 MiB (128^3) sit in L2:
+    no roofline claim there."""
+    cases = [((128, 128, 128), 1, W.C32, 8), ((256, 256, 256), 1, W.C32, 8),
+             ((1024, 1024, 1024), 1, W.C32, 8), ((1024, 1024, 1024), 1, W.C16F, 4),
+             ((4096, 4096), 1, W.C32, 8), ((1 << 20,), 512, W.C32, 8)]
+    out = []
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    for dims, batch, code, eb in cases:
+        elems = batch * int(np.prod(dims))
+        if code == W.C32:
+            xs = torch.view_as_complex(torch.randn((elems, 2), generator=g, device=dev)).contiguous()
+        else:
+            xs = (torch.rand((elems, 2), generator=g, device=dev) * 2 - 1).to(torch.float16)
+        ys = torch.empty_like(xs)
+        norm = W.NORM_PAPER if code == W.C32 else W.NORM_ORTHO
+        f = W.Plan(dims, code, W.FORWARD, batch, norm)
+        i = W.Plan(dims, code, W.INVERSE, batch, norm)
+        npass = f.passes()[0]
+        ms = timed_pairs(f, i, xs, ys, steps, warmup, 1, stream)
+        us = ms / steps * 1e3 / 2
+        nbytes = elems * eb
+        min_passes = 1 if len(dims) == 1 else 2
+        rec = {"dims": list(dims), "batch": batch, "dtype": "complex64" if code == W.C32 else "float16 storage",
+               "us_per_transform": round(us, 2), "passes_used": npass,
+               "gb_per_s": round(npass * 2 * nbytes / (us * 1e-6) / 1e9, 1),
+               "gflops": round(5 * elems * np.log2(elems / batch) / (us * 1e-6) / 1e9, 1)}
+        if nbytes > 256 * 2 ** 20:
+            rec["min_bytes_roofline_frac"] = round(min_passes * 2 * nbytes / (hbm_peak * 1e9) / (us * 1e-6), 4)
+        else:
+            rec["note"] = "array fits in L2: no roofline claim"
+        out.append(rec)
+        f.close()
+        i.close()
+        del xs, ys
+        torch.cuda.empty_cache()
+    return out
+
+
 def ragged_leg(W, dev, stream, reps=5):
     """The ragged configuration (256 uneven 3D shapes from seed 4, N(0,1)):
     one persistent launch replayed from a captured CUDA graph vs one plan
@@ -355,6 +400,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch leg")
+    ap.add_argument("--no-sizes", action="store_true", help="skip the other-sizes leg")
     ap.add_argument("--case", default=None,
                     help="profiling helper: run the default plan of shape D0,D1,D2 "
                          "--case-reps times (complex64 forward, N(0,1) input) and exit")
@@ -480,6 +526,10 @@ def main():
                "h2d_bytes_per_step": 2 * ELEMS * 8, "d2h_bytes_per_step": 2 * ELEMS * 8,
                "steps": esteps, "entry": "wsfft_execute_host (pinned host buffers)"}
 
+    sizes = None
+    if not args.no_sizes and world == 1:
+        sizes = sizes_leg(W, dev, stream, hbm_peak)
+
     ragged = None
     if not args.no_ragged:
         ragged = ragged_leg(W, dev, stream)
@@ -523,6 +573,8 @@ def main():
             line["e2e"] = e2e
         if ragged:
             line["ragged_batch"] = ragged
+        if sizes:
+            line["other_sizes"] = sizes
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -126,8 +126,11 @@ double time_plan(Plan &p, const void *in, void *out, cudaStream_t st) {
     return ok && ms >= 0.f ? ms * 1e3 / 3.0 : -1.0;
 }
 
-// (kind, N) -> extra shapes instantiated by pass_launch.cuh
-std::vector<std::pair<int, int>> shapes_for(int kind, int N) {
+// (kind, N, storage type) -> extra shapes instantiated by pass_launch.cuh
+std::vector<std::pair<int, int>> shapes_for(int kind, int N, int dtype) {
+    // tensor-core DFT-16 stage (16-bit storage only)
+    if (kind == PASS_CONTIG && N == 512 && dtype != WSFFT_C32)
+        return {{32, 16}, {32, 8}, {32, 32}, {16, 8}, {8, 8}, {16, TC_TILE}};
     if (kind == PASS_STRIDED && N == 512)
         return {{32, 16}, {32, 8},  {32, 32}, {16, 16}, {8, 8}, {16, 8}, {16, 32}, {8, PAIR_TILE + 16},
                 {8, PAIR_TILE + 32}, {8, PAIR_TILE + 8}, {16, PAIR_TILE + 16}, {16, PAIR_TILE + 32}};
@@ -192,7 +195,7 @@ extern "C" int wsfft_autotune(wsfft_plan plan, wsfft_stream stream) {
         for (size_t i = 0; i < np; ++i) {
             const PassSpec ps = p->passes[i];
             if (ps.variant || (ps.kind != PASS_CONTIG && ps.kind != PASS_STRIDED)) continue;
-            for (auto sh : shapes_for(ps.kind, ps.N)) {
+            for (auto sh : shapes_for(ps.kind, ps.N, p->dtype)) {
                 Choice c = best;
                 c.variants.push_back({(int)i, sh.first, sh.second});
                 if (apply(*p, c) != WSFFT_SUCCESS) continue;

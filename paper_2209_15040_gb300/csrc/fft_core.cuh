@@ -119,7 +119,7 @@ __device__ __forceinline__ float4 rot16(float4 a) {
     return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
-// In-register R-point forward DFT (R in {1,2,4,8,16}), natural order in and
+// In-register R-point forward DFT (R in {1,2,4,8,16,32}), natural order in and
 // out: split into even and odd halves, transform each, combine with
 // exp(-2*pi*i*k/R).
 template <int R, int K, class V>

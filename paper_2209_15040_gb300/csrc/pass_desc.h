@@ -18,11 +18,21 @@ struct PassArgs {
     float tw_inv;       // four-step twiddle: 2 / L
     int tw_mask;        // four-step twiddle: L - 1
     int64_t tile0;      // strided launches: index of the first tile (set by the launcher)
+    int *status;        // plan's device status word (kernels with bounded waits)
+    uint64_t timeout_ns;  // bound of each wait
 };
 
 // tile codes at or above this select the complex64 pencil-pair strided
 // kernel with (code - PAIR_TILE) pencils per block
 constexpr int PAIR_TILE = 1000;
+// tile code of the tensor-core contiguous superstep (16-bit storage, N = 512)
+constexpr int TC_TILE = 2000;
+// its table (device, 16-byte aligned), in float2 units:
+//   [0, 128)    B_hi of the DFT-16 in the K-major no-swizzle core-matrix byte order
+//   [128, 256)  B_lo, same order
+//   [256, 768)  w512^(k1*n2) at 256 + n2*16 + k1 (k1 in [0,16), n2 in [0,32))
+constexpr int TC_TABLE_TW = 256;
+constexpr int TC_TABLE_FLOAT2 = 768;
 
 enum PassKind {
     PASS_CONTIG = 0,     // one launch, contiguous axis

@@ -4,9 +4,13 @@
 // parallel.
 #pragma once
 
+#include <cudaTypedefs.h>
+
+#include <algorithm>
 #include <type_traits>
 
 #include "pass_kernels.cuh"
+#include "tc_contig.cuh"
 
 namespace wsfft {
 namespace {
@@ -126,11 +130,76 @@ cudaError_t launch_extra(int kind, int N, int E, int tile, const void *in, void 
     return cudaErrorInvalidValue;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library)
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// Tensor-core contiguous superstep (16-bit storage, N = 512).  The input is
+// viewed as rows of 128 bytes (16 rows per pencil); the tensor map loads
+// TC_P pencils per box with 128-byte swizzle.
+template <class S>
+cudaError_t launch_tc_contig(int N, const void *in, void *out, const PassArgs &a, cudaStream_t st) {
+    if constexpr (std::is_same<S, float2>::value) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (N != 512) return cudaErrorInvalidValue;
+        static cudaError_t attr = cudaFuncSetAttribute(tc_contig512_kernel<S>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        if (attr != cudaSuccess) return attr;
+        if (a.npencils <= 0) return cudaSuccess;
+        const int64_t rows = a.npencils * 16;
+        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (rows >= ((int64_t)1 << 31) || ((uintptr_t)in & 15) || !enc || !a.status)
+            return launch_n<512, default_E(512), S>(PASS_CONTIG, false, in, out, a, st);
+        // 128-byte swizzle: the MMA operand layout
+        CUtensorMap map;
+        const cuuint64_t dims[2] = {64, (cuuint64_t)rows};
+        const cuuint64_t strides[1] = {128};
+        const cuuint32_t box[2] = {64, (cuuint32_t)(TC_P * 16)};
+        const cuuint32_t es[2] = {1, 1};
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void *>(in), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        // persistent: one resident block per SM, tiles strided by the grid
+        static int per_sm = 0, sms = 0;
+        if (per_sm == 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_contig512_kernel<S>, TC_THREADS,
+                                                              TC_SMEM) != cudaSuccess)
+                return cudaErrorInvalidValue;
+            per_sm = per_sm > 1 ? 1 : per_sm;  // one block holds all 512 tensor-memory columns
+        }
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        const int64_t ntiles = (a.npencils + TC_P - 1) / TC_P;
+        const int64_t blocks = std::min<int64_t>(ntiles, (int64_t)per_sm * sms);
+        tc_contig512_kernel<S><<<(unsigned)blocks, TC_THREADS, TC_SMEM, st>>>(map, (S *)out, a);
+        return cudaGetLastError();
+    }
+}
+
 }  // namespace
 
 cudaError_t WSFFT_LAUNCH_NAME(int kind, int N, int E, int tile, bool variant, const void *in,
                               void *out, const PassArgs &a, cudaStream_t st) {
     using S = WSFFT_STORE;
+    if (tile == TC_TILE) {
+        if (variant || kind != PASS_CONTIG) return cudaErrorInvalidValue;
+        return launch_tc_contig<S>(N, in, out, a, st);
+    }
     if (tile > 0) {
         if (variant) return cudaErrorInvalidValue;
         return launch_extra<S>(kind, N, E, tile, in, out, a, st);

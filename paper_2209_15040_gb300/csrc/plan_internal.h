@@ -77,6 +77,7 @@ struct Plan {
     int prof_used = 0;                 // launch slots recorded since the last read
 
     const float2 *table(int N, int E);
+    const float2 *tc_table(int N);  // tensor-core contiguous superstep (tc_contig.cuh)
     int build_schedule();
     int build_engine(int64_t n0, int64_t n, bool inv);
     int run(const void *in, void *out, cudaStream_t st);

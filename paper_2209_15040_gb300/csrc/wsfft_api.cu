@@ -94,6 +94,38 @@ std::vector<float2> stage_table(int N, int E) {
     return t;
 }
 
+// Table of the tensor-core contiguous superstep at N = 512 (layout in
+// tc_contig.cuh): the DFT-16 matrix B[n = 2*k1 + part][k = n1] = (Re, Im)
+// w16^(n1*k1) as 16-bit high parts and 16-bit remainders in the K-major
+// core-matrix byte order, then the inter-stage twiddles w512^(k1*n2).
+std::vector<float2> tc_table_host(int dtype) {
+    std::vector<float2> t(TC_TABLE_FLOAT2);
+    uint16_t *hi = reinterpret_cast<uint16_t *>(t.data());
+    uint16_t *lo = hi + 512;
+    for (int n = 0; n < 32; ++n)
+        for (int k = 0; k < 16; ++k) {
+            const int k1 = n / 2, part = n % 2, n1 = k;
+            const float2 w = host_root((int64_t)n1 * k1, 16);
+            const float v = part ? w.y : w.x;
+            uint16_t h, l;
+            if (dtype == WSFFT_C16BF) {
+                const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+                h = __bfloat16_as_ushort(hb);
+                l = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(hb)));
+            } else {
+                const __half hh = __float2half_rn(v);
+                h = __half_as_ushort(hh);
+                l = __half_as_ushort(__float2half_rn(v - __half2float(hh)));
+            }
+            const int off = (n / 8) * 256 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;  // bytes
+            hi[off / 2] = h;
+            lo[off / 2] = l;
+        }
+    for (int n2 = 0; n2 < 32; ++n2)
+        for (int k1 = 0; k1 < 16; ++k1) t[TC_TABLE_TW + n2 * 16 + k1] = host_root((int64_t)k1 * n2, 512);
+    return t;
+}
+
 float axis_scale(int64_t n, int dir, int norm) {
     if (norm == WSFFT_NORM_PAPER) return dir == WSFFT_INVERSE ? (float)(1.0 / (double)n) : 1.f;
     if (norm == WSFFT_NORM_ORTHO) return (float)(1.0 / std::sqrt((double)n));
@@ -148,6 +180,22 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? WSFFT_SUCCESS : WSFFT
 }  // namespace
 
 namespace wsfft {
+
+const float2 *Plan::tc_table(int N) {
+    if (N != 512 || dtype == WSFFT_C32) return nullptr;
+    auto key = std::make_pair(N, TC_TILE);
+    auto it = tables.find(key);
+    if (it != tables.end()) return it->second;
+    std::vector<float2> h = tc_table_host(dtype);
+    float2 *d = nullptr;
+    if (cudaMalloc(&d, h.size() * sizeof(float2)) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(d, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    tables[key] = d;
+    return d;
+}
 
 const float2 *Plan::table(int N, int E) {
     auto key = std::make_pair(N, E);
@@ -417,7 +465,7 @@ int Plan::build_schedule() {
     }
     for (auto &p : passes) {
         if (p.N > 4096 || !is_pow2(p.N)) return WSFFT_ERR_INVALID_SIZE;
-        p.tw = table(p.N, p.E);
+        p.tw = p.tile == TC_TILE ? tc_table(p.N) : table(p.N, p.E);
         if (!p.tw) return WSFFT_ERR_ALLOC;
     }
     if (work_elems > work_cap) {
@@ -516,6 +564,8 @@ int Plan::run(const void *in, void *out, cudaStream_t st) {
             a.trans_rows = p.trans_rows;
             a.tw_inv = p.twid_len ? (float)(2.0 / (double)p.twid_len) : 0.f;
             a.tw_mask = p.twid_len ? (int)(p.twid_len - 1) : 0;
+            a.status = d_status;
+            a.timeout_ns = (uint64_t)wait_timeout_ns;
             prof_begin(st);
             cudaError_t e = launch(dtype, p, src, dst, a, st);
             prof_end(st);

@@ -17,6 +17,7 @@ from tests._helpers import DT, TOL, seeded, to_device, to_host_c128
 pytestmark = pytest.mark.gpu
 
 PAIR = 1000  # tile codes from PAIR_TILE on select the pencil-pair kernel
+TC = 2000    # tile code of the tensor-core contiguous superstep (16-bit storage, 512)
 
 # (values per thread, tile) shapes per axis length
 CONTIG = {512: [(32, 16), (32, 8), (32, 32), (16, 8), (8, 8)], 256: [(8, 8)]}
@@ -36,25 +37,25 @@ def _lib():
 _cache = {}
 
 
-def _case(shape_full, rank, dtype, seed):
-    key = (shape_full, rank, dtype, seed)
+def _case(shape_full, rank, dtype, seed, direction=W.FORWARD):
+    key = (shape_full, rank, dtype, seed, direction)
     if key not in _cache:
         xs, xc = seeded(shape_full, seed, "uniform", dtype)
         norm = W.NORM_PAPER if dtype == "c32" else W.NORM_ORTHO
-        _cache[key] = (to_device(xs, dtype), oracle.fftn(xc, rank=rank, sign=W.FORWARD, norm=norm),
+        _cache[key] = (to_device(xs, dtype), oracle.fftn(xc, rank=rank, sign=direction, norm=norm),
                        norm)
     return _cache[key]
 
 
-def run_variant(shape_full, rank, dtype, settings, seed=5):
-    x, ref, norm = _case(shape_full, rank, dtype, seed)
+def run_variant(shape_full, rank, dtype, settings, seed=5, direction=W.FORWARD, inplace=False):
+    x, ref, norm = _case(shape_full, rank, dtype, seed, direction)
     dims = shape_full[len(shape_full) - rank:]
     batch = int(np.prod(shape_full[:len(shape_full) - rank], dtype=np.int64))
-    plan = W.Plan(dims, DT[dtype], W.FORWARD, batch, norm)
+    plan = W.Plan(dims, DT[dtype], direction, batch, norm)
     for pass_index, e, tile in settings:
         plan.set_pass_variant(pass_index, e, tile)
-    out = torch.empty_like(x)
-    plan.execute(x.data_ptr(), out.data_ptr())
+    out = x.clone() if inplace else torch.empty_like(x)
+    plan.execute(out.data_ptr() if inplace else x.data_ptr(), out.data_ptr())
     torch.cuda.synchronize()
     assert plan.sync_status() == W.SUCCESS
     plan.close()
@@ -123,3 +124,26 @@ def test_1024_shapes(dtype):
     for sh in STRIDED[1024]:
         run_variant((1024, 4, 16), 3, dtype, [(2, *sh)])
 
+
+
+# -- tensor-core contiguous superstep (DFT-16 on tcgen05, DFT-32 in registers)
+
+@pytest.mark.parametrize("dtype", ["c16f", "c16bf"])
+@pytest.mark.parametrize("direction", [W.FORWARD, W.INVERSE])
+@pytest.mark.parametrize("shape_full,rank", [((64, 8, 512), 3), ((37, 512), 1), ((3, 16, 512), 2),
+                                             ((1, 512), 1)])
+def test_tensor_core_contig_512(dtype, direction, shape_full, rank):
+    # 37 and 3*16 = 48 pencils: partial last tiles (the TMA box reads zeros past the end)
+    run_variant(shape_full, rank, dtype, [(0, 16, TC)], direction=direction)
+
+
+@pytest.mark.parametrize("dtype", ["c16f", "c16bf"])
+def test_tensor_core_contig_512_in_place(dtype):
+    run_variant((16, 16, 512), 3, dtype, [(0, 16, TC)], direction=W.INVERSE, inplace=True)
+
+
+def test_tensor_core_contig_rejects_complex64():
+    plan = W.Plan((8, 512), W.C32, W.FORWARD, 1)
+    with pytest.raises(RuntimeError):
+        plan.set_pass_variant(0, 16, TC)
+    plan.close()
