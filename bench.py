@@ -361,13 +361,20 @@ def run_case(args):
     from paper_2209_15040_gb300 import wsfft as W
     _build.build_library()
     dims = tuple(int(v) for v in args.case.split(","))
-    x = torch.view_as_complex(torch.randn(dims + (2,), device="cuda")).contiguous()
+    code = {"c32": W.C32, "c16f": W.C16F, "c16bf": W.C16BF}[args.case_dtype]
+    if code == W.C32:
+        x = torch.view_as_complex(torch.randn(dims + (2,), device="cuda")).contiguous()
+    else:
+        x = torch.randn(dims + (2,), device="cuda").to(torch.float16 if code == W.C16F else torch.bfloat16)
     y = torch.empty_like(x)
-    plan = W.Plan(dims, W.C32, W.FORWARD, 1)
+    plan = W.Plan(dims, code, W.FORWARD, 1)
+    if args.case_variant:
+        plan.set_pass_variant(*(int(v) for v in args.case_variant.split(",")))
     for _ in range(args.case_reps):
         plan.execute(x.data_ptr(), y.data_ptr())
     torch.cuda.synchronize()
-    print(json.dumps({"case": list(dims), "passes": plan.passes()[0], "reps": args.case_reps}))
+    print(json.dumps({"case": list(dims), "dtype": args.case_dtype, "variant": args.case_variant,
+                      "passes": plan.passes()[0], "reps": args.case_reps, "status": plan.sync_status()}))
     plan.close()
 
 
@@ -403,8 +410,11 @@ def main():
     ap.add_argument("--no-sizes", action="store_true", help="skip the other-sizes leg")
     ap.add_argument("--case", default=None,
                     help="profiling helper: run the default plan of shape D0,D1,D2 "
-                         "--case-reps times (complex64 forward, N(0,1) input) and exit")
+                         "--case-reps times (forward, N(0,1) input, storage --case-dtype) and exit")
     ap.add_argument("--case-reps", type=int, default=3)
+    ap.add_argument("--case-dtype", default="c32", choices=["c32", "c16f", "c16bf"])
+    ap.add_argument("--case-variant", default=None,
+                    help="PASS,E,TILE: kernel shape of one pass (wsfft_plan_set_pass_variant)")
     ap.add_argument("--sweep", action="store_true",
                     help="batched 1D pencil sweep n = 16..4096 over 2^27 complex elements "
                          "(FP32 and FP16 storage); one JSON line per point, then exit")
