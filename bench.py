@@ -218,7 +218,8 @@ def run_reference(args, world, rank):
 
 def sizes_leg(W, dev, stream, hbm_peak, steps=20, warmup=3):
     """The other transform sizes of the workload family, each timed like the
-    main step ((FFT + IFFT)/2, data resident, CUDA events on the stream):
+    main step ((FFT + IFFT)/2 per execute of the whole batch, data resident,
+    CUDA events on the stream):
     cubes 128^3, 256^3 and 1024^3 (complex64 and float16 storage), 2D
     4096 x 4096 and 1D 2^20 x batch 512 (complex64).  GB/s counts one read and
     one write of the array per launch; the minimum-bytes fraction uses 2
@@ -246,7 +247,7 @@ def sizes_leg(W, dev, stream, hbm_peak, steps=20, warmup=3):
         nbytes = elems * eb
         min_passes = 1 if len(dims) == 1 else 2
         rec = {"dims": list(dims), "batch": batch, "dtype": "complex64" if code == W.C32 else "float16 storage",
-               "us_per_transform": round(us, 2), "passes_used": npass,
+               "us_per_execute": round(us, 2), "us_per_transform": round(us / batch, 3), "passes_used": npass,
                "gb_per_s": round(npass * 2 * nbytes / (us * 1e-6) / 1e9, 1),
                "gflops": round(5 * elems * np.log2(elems / batch) / (us * 1e-6) / 1e9, 1)}
         if nbytes > 256 * 2 ** 20:
