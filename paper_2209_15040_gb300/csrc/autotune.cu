@@ -194,7 +194,7 @@ extern "C" int wsfft_autotune(wsfft_plan plan, wsfft_stream stream) {
         const size_t np = p->passes.size();
         for (size_t i = 0; i < np; ++i) {
             const PassSpec ps = p->passes[i];
-            if (ps.variant || (ps.kind != PASS_CONTIG && ps.kind != PASS_STRIDED)) continue;
+            if (ps.kind != PASS_CONTIG && ps.kind != PASS_STRIDED) continue;
             for (auto sh : shapes_for(ps.kind, ps.N, p->dtype)) {
                 Choice c = best;
                 c.variants.push_back({(int)i, sh.first, sh.second});

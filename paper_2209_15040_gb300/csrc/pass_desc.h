@@ -15,7 +15,9 @@ struct PassArgs {
     float conj_in;      // +1, or -1 to conjugate every loaded value
     float sx, sy;       // store scale of re and im (sy = -sx conjugates)
     int64_t trans_rows; // contiguous transposed store: rows per transform
-    float tw_inv;       // four-step twiddle: 2 / L
+    const float2 *tw_hi;  // four-step twiddle w_L^m = tw_hi[m >> tw_shift] * tw_lo[m & (2^tw_shift - 1)]
+    const float2 *tw_lo;
+    int tw_shift;
     int tw_mask;        // four-step twiddle: L - 1
     int64_t tile0;      // strided launches: index of the first tile (set by the launcher)
     int *status;        // plan's device status word (kernels with bounded waits)

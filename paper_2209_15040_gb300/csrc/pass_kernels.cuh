@@ -188,8 +188,9 @@ struct StridedAcc {
     Epi epi;
     bool active;
     int twq;        // four-step: inner index of this pencil
-    float tw_inv;   // four-step: 2 / (length of the long transform)
-    int tw_mask;    // four-step: length - 1
+    const float2 *tw_hi, *tw_lo;  // four-step: w_L^m = tw_hi[m >> tw_shift] * tw_lo[m & low mask]
+    int tw_shift;
+    int tw_mask;    // four-step: L - 1 (L = length of the long transform)
     __device__ __forceinline__ float2 gload(int k) const {
         float2 v = active ? Cvt<S>::template load<LOP>(in + (int64_t)k * stride) : make_float2(0.f, 0.f);
         if constexpr (!PLAIN) v.y *= ci;
@@ -197,11 +198,10 @@ struct StridedAcc {
     }
     __device__ __forceinline__ void gstore(int k, float2 v) const {
         if constexpr (TWID) {
-            // w_L^(q*k), L = tw_mask + 1; the angle 2*m/L is exact in float
+            // w_L^(q*k), L = tw_mask + 1, from two tables of the host's
+            // long-double roots: w_L^m = w_L^(m_hi << shift) * w_L^(m_lo)
             const int m = (twq * k) & tw_mask;
-            float s, c;
-            sincospif((float)m * tw_inv, &s, &c);
-            v = cmul(v, make_float2(c, -s));
+            v = cmul(v, cmul(__ldg(&tw_hi[m >> tw_shift]), __ldg(&tw_lo[m & ((1 << tw_shift) - 1)])));
         }
         if constexpr (!PLAIN) v = make_float2(v.x * epi.sx, v.y * epi.sy);
         if (active) Cvt<S>::template store<SOP>(out + (int64_t)k * stride, v);
@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(W *(N / E), strided_min_blocks(W *(N / E), E))
     acc.epi = {a.sx, a.sy};
     acc.active = q < a.npencils;
     acc.twq = (int)i;
-    acc.tw_inv = a.tw_inv;
+    acc.tw_hi = a.tw_hi;
+    acc.tw_lo = a.tw_lo;
+    acc.tw_shift = a.tw_shift;
     acc.tw_mask = a.tw_mask;
     pencil_fft<N, E>(acc, t, a.tw);
 }

@@ -111,6 +111,9 @@ cudaError_t launch_extra(int kind, int N, int E, int tile, const void *in, void 
     WSFFT_XS(256, 16, 32)
     WSFFT_XS(256, 8, 16)
     WSFFT_XS(1024, 16, 8)
+    WSFFT_XS(1024, 32, 8)
+    WSFFT_XS(1024, 32, 16)
+    WSFFT_XC(1024, 32, 8)
     WSFFT_XC(512, 16, 8)
     WSFFT_XC(512, 32, 16)
     WSFFT_XC(512, 32, 8)
@@ -127,6 +130,20 @@ cudaError_t launch_extra(int kind, int N, int E, int tile, const void *in, void 
     }
 #undef WSFFT_XC
 #undef WSFFT_XS
+    return cudaErrorInvalidValue;
+}
+
+// Extra shapes of the variant passes (four-step twiddle on a strided store,
+// transposed contiguous store).
+template <class S>
+cudaError_t launch_extra_variant(int kind, int N, int E, int tile, const void *in, void *out,
+                                 const PassArgs &a, cudaStream_t st) {
+    if (kind == PASS_STRIDED && N == 1024 && E == 32 && tile == 8)
+        return launch_strided<1024, 32, 8, S, true>(in, out, a, st);
+    if (kind == PASS_STRIDED && N == 1024 && E == 32 && tile == 16)
+        return launch_strided<1024, 32, 16, S, true>(in, out, a, st);
+    if (kind == PASS_CONTIG && N == 1024 && E == 32 && tile == 8)
+        return launch_contig<1024, 32, 8, S, true>(in, out, a, st);
     return cudaErrorInvalidValue;
 }
 
@@ -201,7 +218,7 @@ cudaError_t WSFFT_LAUNCH_NAME(int kind, int N, int E, int tile, bool variant, co
         return launch_tc_contig<S>(N, in, out, a, st);
     }
     if (tile > 0) {
-        if (variant) return cudaErrorInvalidValue;
+        if (variant) return launch_extra_variant<S>(kind, N, E, tile, in, out, a, st);
         return launch_extra<S>(kind, N, E, tile, in, out, a, st);
     }
 #define WSFFT_CASE(n)                                                              \

@@ -27,6 +27,7 @@ struct PassSpec {
     float scale;
     int64_t trans_rows;          // transposed store: rows per transform
     int64_t twid_len;            // four-step twiddle: length of the long axis
+    int twid_shift;              // four-step twiddle: bits of the low table index
     const float2 *tw;            // device stage-twiddle table
     const float2 *tw2;           // fused passes: table of the strided tiles, if it differs
     // persistent engine passes (kind PASS_ENGINE_A / PASS_ENGINE_B)
@@ -78,6 +79,8 @@ struct Plan {
 
     const float2 *table(int N, int E);
     const float2 *tc_table(int N);  // tensor-core contiguous superstep (tc_contig.cuh)
+    std::map<int64_t, float2 *> fs_tables;        // four-step twiddle tables per long length
+    const float2 *fourstep_table(int64_t L, int shift);
     int build_schedule();
     int build_engine(int64_t n0, int64_t n, bool inv);
     int run(const void *in, void *out, cudaStream_t st);

@@ -102,7 +102,9 @@ __device__ __forceinline__ void rag_strided(const RagInst &I, int d, int tile, c
     acc.epi = Epi{sx, sy};
     acc.active = q < npen;
     acc.twq = 0;
-    acc.tw_inv = 0.f;
+    acc.tw_hi = nullptr;
+    acc.tw_lo = nullptr;
+    acc.tw_shift = 0;
     acc.tw_mask = 0;
     (void)T;
     pencil_fft<N, rag_E(N)>(acc, t, tw);

@@ -197,6 +197,26 @@ const float2 *Plan::tc_table(int N) {
     return d;
 }
 
+// Four-step inter-superstep twiddles w_L^m, m < L, as two tables: the high
+// part w_L^(i << shift) for i < L >> shift, then the low part w_L^j for
+// j < 2^shift (w_L^m is their product; both from host_root).
+const float2 *Plan::fourstep_table(int64_t L, int shift) {
+    auto it = fs_tables.find(L);
+    if (it != fs_tables.end()) return it->second;
+    const int64_t nh = L >> shift, nl = (int64_t)1 << shift;
+    std::vector<float2> h((size_t)(nh + nl));
+    for (int64_t i = 0; i < nh; ++i) h[(size_t)i] = host_root(i << shift, L);
+    for (int64_t j = 0; j < nl; ++j) h[(size_t)(nh + j)] = host_root(j, L);
+    float2 *d = nullptr;
+    if (cudaMalloc(&d, h.size() * sizeof(float2)) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(d, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    fs_tables[L] = d;
+    return d;
+}
+
 const float2 *Plan::table(int N, int E) {
     auto key = std::make_pair(N, E);
     auto it = tables.find(key);
@@ -381,6 +401,11 @@ int Plan::build_schedule() {
         a.kind = PASS_STRIDED;
         a.N = (int)n2;
         a.E = default_E((int)n2);
+        if (n2 == 1024 && dtype == WSFFT_C32) {
+            // measured fastest at n = 2^20: 32 values per thread, 16 pencils per block
+            a.E = 32;
+            a.tile = 16;
+        }
         a.variant = true;
         a.inner = n1;
         a.npencils_per_batch = n1;
@@ -390,11 +415,17 @@ int Plan::build_schedule() {
         a.conj_out = false;
         a.scale = 1.f;
         a.twid_len = n;
+        a.twid_shift = (lg + 1) / 2;
         a.transform_elems = n;
         PassSpec b{};
         b.kind = PASS_CONTIG;
         b.N = (int)n1;
         b.E = default_E((int)n1);
+        if (n1 == 1024 && dtype == WSFFT_C32) {
+            // one warp per pencil (32 values per thread), 8 pencils per block
+            b.E = 32;
+            b.tile = 8;
+        }
         b.variant = true;
         b.inner = 1;
         b.npencils_per_batch = n2;
@@ -425,6 +456,14 @@ int Plan::build_schedule() {
                 // on load of the inverse)
                 p.E = 16;
                 p.tile = 8;
+            }
+            if (p.N == 1024 && dtype == WSFFT_C32) {
+                // measured at 1024^3: 32 values per thread (radix 32 x 32, one
+                // exchange); contiguous: one warp per pencil, 8 per block;
+                // strided: 8 pencils per block at strides below 2^17 elements,
+                // 16 beyond (rows of 64 or 128 bytes)
+                p.E = 32;
+                p.tile = p.kind == PASS_CONTIG ? 8 : (inner >= ((int64_t)1 << 17) ? 16 : 8);
             }
             if (p.kind == PASS_STRIDED && p.N == 512 && inner % 16 == 0) {
                 // measured fastest at 512^3: complex64 with 32 values per
@@ -457,7 +496,7 @@ int Plan::build_schedule() {
         }
     }
     for (auto &kv : overrides) {
-        if (kv.first < (int)passes.size() && !passes[kv.first].variant &&
+        if (kv.first < (int)passes.size() &&
             (passes[kv.first].kind == PASS_CONTIG || passes[kv.first].kind == PASS_STRIDED)) {
             passes[kv.first].E = kv.second.first;
             passes[kv.first].tile = kv.second.second;
@@ -466,6 +505,10 @@ int Plan::build_schedule() {
     for (auto &p : passes) {
         if (p.N > 4096 || !is_pow2(p.N)) return WSFFT_ERR_INVALID_SIZE;
         p.tw = p.tile == TC_TILE ? tc_table(p.N) : table(p.N, p.E);
+        if (p.twid_len) {
+            p.tw2 = fourstep_table(p.twid_len, p.twid_shift);
+            if (!p.tw2) return WSFFT_ERR_ALLOC;
+        }
         if (!p.tw) return WSFFT_ERR_ALLOC;
     }
     if (work_elems > work_cap) {
@@ -562,7 +605,9 @@ int Plan::run(const void *in, void *out, cudaStream_t st) {
             a.sx = p.scale;
             a.sy = p.conj_out ? -p.scale : p.scale;
             a.trans_rows = p.trans_rows;
-            a.tw_inv = p.twid_len ? (float)(2.0 / (double)p.twid_len) : 0.f;
+            a.tw_hi = p.twid_len ? p.tw2 : nullptr;
+            a.tw_lo = p.twid_len ? p.tw2 + (p.twid_len >> p.twid_shift) : nullptr;
+            a.tw_shift = p.twid_len ? p.twid_shift : 0;
             a.tw_mask = p.twid_len ? (int)(p.twid_len - 1) : 0;
             a.status = d_status;
             a.timeout_ns = (uint64_t)wait_timeout_ns;
@@ -595,6 +640,7 @@ Plan::~Plan() {
     if (d_items) cudaFree(d_items);
     if (d_ctr) cudaFree(d_ctr);
     for (auto &kv : tables) cudaFree(kv.second);
+    for (auto &kv : fs_tables) cudaFree(kv.second);
     if (work) cudaFree(work);
     if (host_buf) cudaFree(host_buf);
     if (d_status) cudaFree(d_status);
@@ -726,7 +772,7 @@ int wsfft_plan_set_pass_variant(wsfft_plan plan, int pass, int values_per_thread
         return p->build_schedule();
     }
     const PassSpec &ps = p->passes[pass];
-    if (ps.variant || (ps.kind != PASS_CONTIG && ps.kind != PASS_STRIDED)) return WSFFT_ERR_UNSUPPORTED;
+    if (ps.kind != PASS_CONTIG && ps.kind != PASS_STRIDED) return WSFFT_ERR_UNSUPPORTED;
     // probe: is this shape instantiated?  (an empty launch returns before running)
     PassArgs a{};
     a.npencils = 0;

@@ -20,9 +20,9 @@ PAIR = 1000  # tile codes from PAIR_TILE on select the pencil-pair kernel
 TC = 2000    # tile code of the tensor-core contiguous superstep (16-bit storage, 512)
 
 # (values per thread, tile) shapes per axis length
-CONTIG = {512: [(32, 16), (32, 8), (32, 32), (16, 8), (8, 8)], 256: [(8, 8)]}
+CONTIG = {512: [(32, 16), (32, 8), (32, 32), (16, 8), (8, 8)], 256: [(8, 8)], 1024: [(32, 8)]}
 STRIDED = {512: [(32, 16), (32, 8), (32, 32), (16, 16), (8, 8), (16, 8), (16, 32)],
-           256: [(16, 32), (8, 16)], 1024: [(16, 8)]}
+           256: [(16, 32), (8, 16)], 1024: [(16, 8), (32, 8), (32, 16)]}
 PAIRS = {512: [(8, PAIR + 16), (8, PAIR + 32), (8, PAIR + 8), (16, PAIR + 16), (16, PAIR + 32)],
          256: [(8, PAIR + 16)]}
 
@@ -121,8 +121,21 @@ def test_256_shapes(dtype):
 
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_1024_shapes(dtype):
+    for sh in CONTIG[1024]:
+        run_variant((4, 8, 1024), 3, dtype, [(0, *sh)])
+        run_variant((5, 1024), 1, dtype, [(0, *sh)])  # ragged: 5 pencils
     for sh in STRIDED[1024]:
         run_variant((1024, 4, 16), 3, dtype, [(2, *sh)])
+        run_variant((3, 1024, 2), 2, dtype, [(1, *sh)])  # ragged: 6 pencils
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("settings", [[(0, 32, 8)], [(0, 32, 16)], [(1, 32, 8)], [(0, 32, 16), (1, 32, 8)]])
+def test_four_step_shapes(dtype, settings):
+    # 1D n = 2^20 = 1024 x 1024: pass 0 strided with the inter-step twiddle,
+    # pass 1 contiguous with the transposed store
+    run_variant((2, 1 << 20), 1, dtype, settings)
+    run_variant((1, 1 << 20), 1, dtype, settings, direction=W.INVERSE)
 
 
 
