@@ -119,9 +119,15 @@ int wsfft_execute(wsfft_plan plan, const void *in, void *out, wsfft_stream strea
 
 /* Same transform with HOST buffers: copies host_in to a plan-owned device
  * buffer, transforms, copies back to host_out, and waits for the stream.
- * host_in/host_out should be page-locked for full copy speed.  The first
- * call allocates the device buffer (2 * batch * prod(dims) elements).
- * Errors: as wsfft_execute, plus ALLOC. */
+ * host_in/host_out should be page-locked for full copy speed; they may be
+ * the same buffer.  For rank-3 plans with one launch per superstep the
+ * copies overlap the compute: slab chunks come in on a second stream (owned
+ * by the plan) and are transformed along the last axis as they arrive, the
+ * first axis is transformed over the whole array, and the middle axis slab
+ * chunk by slab chunk, each chunk copied back as soon as it is done (the
+ * result equals wsfft_execute's up to rounding: the axes are taken in
+ * another order).  The first call allocates the device buffer
+ * (batch * prod(dims) elements).  Errors: as wsfft_execute, plus ALLOC. */
 int wsfft_execute_host(wsfft_plan plan, const void *host_in, void *host_out,
                        wsfft_stream stream);
 

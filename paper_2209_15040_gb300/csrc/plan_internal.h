@@ -10,6 +10,8 @@
 
 namespace wsfft {
 
+struct PassArgs;
+
 enum { SRC_IN = 0, SRC_OUT = 1, SRC_WORK = 2 };
 enum { DST_OUT = 0, DST_WORK = 1 };
 
@@ -52,6 +54,8 @@ struct Plan {
     int64_t work_cap = 0;
     void *work = nullptr;
     void *host_buf = nullptr;  // device buffer for wsfft_execute_host
+    cudaStream_t copy_stream = nullptr;  // wsfft_execute_host: copies overlapping the supersteps
+    std::vector<cudaEvent_t> pipe_ev;
     int *d_status = nullptr;   // device status word (timeouts)
     // persistent engine state
     int sm_count = 0;
@@ -78,12 +82,15 @@ struct Plan {
     int prof_used = 0;                 // launch slots recorded since the last read
 
     const float2 *table(int N, int E);
+    PassArgs pass_args(const PassSpec &p, int64_t npencils) const;
     const float2 *tc_table(int N);  // tensor-core contiguous superstep (tc_contig.cuh)
     std::map<int64_t, float2 *> fs_tables;        // four-step twiddle tables per long length
     const float2 *fourstep_table(int64_t L, int shift);
     int build_schedule();
     int build_engine(int64_t n0, int64_t n, bool inv);
     int run(const void *in, void *out, cudaStream_t st);
+    bool can_pipeline_host() const;
+    int run_host_pipelined(const void *hin, void *hout, cudaStream_t st);
     // bracket one kernel launch with profiling events (no-op when off)
     void prof_begin(cudaStream_t st);
     void prof_end(cudaStream_t st);

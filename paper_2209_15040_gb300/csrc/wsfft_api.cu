@@ -596,26 +596,115 @@ int Plan::run(const void *in, void *out, cudaStream_t st) {
                               : p.src == SRC_OUT ? (const char *)out + off
                                                  : (const char *)work;
             char *dst = p.dst == DST_OUT ? (char *)out + off : (char *)work;
-            PassArgs a{};
-            a.npencils = p.npencils_per_batch * nb;
-            a.inner = p.inner;
-            a.log_inner = ilog2(p.inner);
-            a.tw = p.tw;
-            a.conj_in = p.conj_in ? -1.f : 1.f;
-            a.sx = p.scale;
-            a.sy = p.conj_out ? -p.scale : p.scale;
-            a.trans_rows = p.trans_rows;
-            a.tw_hi = p.twid_len ? p.tw2 : nullptr;
-            a.tw_lo = p.twid_len ? p.tw2 + (p.twid_len >> p.twid_shift) : nullptr;
-            a.tw_shift = p.twid_len ? p.twid_shift : 0;
-            a.tw_mask = p.twid_len ? (int)(p.twid_len - 1) : 0;
-            a.status = d_status;
-            a.timeout_ns = (uint64_t)wait_timeout_ns;
+            const PassArgs a = pass_args(p, p.npencils_per_batch * nb);
             prof_begin(st);
             cudaError_t e = launch(dtype, p, src, dst, a, st);
             prof_end(st);
             if (e != cudaSuccess) return e == cudaErrorInvalidValue ? WSFFT_ERR_UNSUPPORTED : WSFFT_ERR_CUDA;
         }
+    }
+    return WSFFT_SUCCESS;
+}
+
+PassArgs Plan::pass_args(const PassSpec &p, int64_t npencils) const {
+    PassArgs a{};
+    a.npencils = npencils;
+    a.inner = p.inner;
+    a.log_inner = ilog2(p.inner);
+    a.tw = p.tw;
+    a.conj_in = p.conj_in ? -1.f : 1.f;
+    a.sx = p.scale;
+    a.sy = p.conj_out ? -p.scale : p.scale;
+    a.trans_rows = p.trans_rows;
+    a.tw_hi = p.twid_len ? p.tw2 : nullptr;
+    a.tw_lo = p.twid_len ? p.tw2 + (p.twid_len >> p.twid_shift) : nullptr;
+    a.tw_shift = p.twid_len ? p.twid_shift : 0;
+    a.tw_mask = p.twid_len ? (int)(p.twid_len - 1) : 0;
+    a.status = d_status;
+    a.timeout_ns = (uint64_t)wait_timeout_ns;
+    return a;
+}
+
+// Host buffers, rank 3 with one launch per superstep: the copies overlap the
+// supersteps.  Slab chunks (along the first axis) are copied in on a second
+// stream and the z superstep of each chunk (slab-local) runs as soon as the
+// chunk has arrived; the x superstep, which needs every slab, runs over the
+// whole array; then the y superstep (slab-local again) runs chunk by chunk
+// and each finished chunk goes back to the host with one contiguous copy
+// while the next is transformed.  The supersteps are taken in the order z, x,
+// y (the order of axes is free, Section 1).  The data crosses the host link
+// once in each direction; the x superstep and one chunk's z and y are the
+// only compute not hidden behind a copy.  (Chunking the x superstep instead
+// would need strided 2D copies back, measured 17% slower than contiguous
+// ones on this link.)
+bool Plan::can_pipeline_host() const {
+    if (ragged || rank != 3 || chunk != batch || passes.size() != 3 || dims[0] < 2) return false;
+    if (passes[0].kind != PASS_CONTIG || passes[1].kind != PASS_STRIDED || passes[2].kind != PASS_STRIDED)
+        return false;
+    for (const auto &p : passes)
+        if (p.variant || p.src == SRC_WORK || p.dst == DST_WORK) return false;
+    return true;
+}
+
+int Plan::run_host_pipelined(const void *hin, void *hout, cudaStream_t st) {
+    constexpr int K = 8;  // chunks per direction
+    if (!copy_stream) {
+        if (cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            copy_stream = nullptr;
+            return WSFFT_ERR_CUDA;
+        }
+        pipe_ev.resize(2 * K + 2);
+        for (auto &e : pipe_ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return WSFFT_ERR_CUDA;
+    }
+    const int64_t eb = elem_bytes(dtype);
+    const int64_t n0 = dims[0], I = dims[1] * dims[2];
+    const int kz = (int)std::min<int64_t>(K, n0);
+    cudaEvent_t ev_start = pipe_ev[2 * K], ev_done = pipe_ev[2 * K + 1];
+    char *dev = (char *)host_buf;
+    auto ck = [](cudaError_t e) { return e == cudaSuccess; };
+    for (int64_t b = 0; b < batch; ++b) {
+        const char *hb = (const char *)hin + b * elems * eb;
+        char *ho = (char *)hout + b * elems * eb;
+        char *db = dev + b * elems * eb;
+        if (!ck(cudaEventRecord(ev_start, st)) || !ck(cudaStreamWaitEvent(copy_stream, ev_start, 0)))
+            return WSFFT_ERR_CUDA;
+        auto run_pass = [&](const PassSpec &p, char *ptr, int64_t npencils) {
+            const PassArgs a = pass_args(p, npencils);
+            prof_begin(st);
+            cudaError_t e = launch(dtype, p, ptr, ptr, a, st);
+            prof_end(st);
+            return e == cudaSuccess ? WSFFT_SUCCESS : e == cudaErrorInvalidValue ? WSFFT_ERR_UNSUPPORTED : WSFFT_ERR_CUDA;
+        };
+        // in: slab chunks, each followed by its z superstep
+        for (int c = 0; c < kz; ++c) {
+            const int64_t s0 = c * n0 / kz, s1 = (c + 1) * n0 / kz;
+            const int64_t o = s0 * I * eb, bytes = (s1 - s0) * I * eb;
+            if (!ck(cudaMemcpyAsync(db + o, hb + o, (size_t)bytes, cudaMemcpyHostToDevice, copy_stream)) ||
+                !ck(cudaEventRecord(pipe_ev[c], copy_stream)) || !ck(cudaStreamWaitEvent(st, pipe_ev[c], 0)))
+                return WSFFT_ERR_CUDA;
+            const int rc = run_pass(passes[0], db + o, (s1 - s0) * dims[1]);
+            if (rc != WSFFT_SUCCESS) return rc;
+        }
+        // the x superstep over the whole array; the inverse's conjugation of
+        // the output moves to the y superstep, which now runs last
+        PassSpec px = passes[2], py = passes[1];
+        py.conj_out = px.conj_out;
+        px.conj_out = false;
+        int rc = run_pass(px, db, I);
+        if (rc != WSFFT_SUCCESS) return rc;
+        // out: the y superstep of each slab chunk, then its copy back
+        for (int c = 0; c < kz; ++c) {
+            const int64_t s0 = c * n0 / kz, s1 = (c + 1) * n0 / kz;
+            const int64_t o = s0 * I * eb, bytes = (s1 - s0) * I * eb;
+            rc = run_pass(py, db + o, (s1 - s0) * dims[2]);
+            if (rc != WSFFT_SUCCESS) return rc;
+            if (!ck(cudaEventRecord(pipe_ev[K + c], st)) || !ck(cudaStreamWaitEvent(copy_stream, pipe_ev[K + c], 0)) ||
+                !ck(cudaMemcpyAsync(ho + o, db + o, (size_t)bytes, cudaMemcpyDeviceToHost, copy_stream)))
+                return WSFFT_ERR_CUDA;
+        }
+        if (!ck(cudaEventRecord(ev_done, copy_stream)) || !ck(cudaStreamWaitEvent(st, ev_done, 0)))
+            return WSFFT_ERR_CUDA;
     }
     return WSFFT_SUCCESS;
 }
@@ -643,6 +732,8 @@ Plan::~Plan() {
     for (auto &kv : fs_tables) cudaFree(kv.second);
     if (work) cudaFree(work);
     if (host_buf) cudaFree(host_buf);
+    for (auto e : pipe_ev) cudaEventDestroy(e);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
     if (d_status) cudaFree(d_status);
 }
 
@@ -741,6 +832,11 @@ int wsfft_execute_host(wsfft_plan plan, const void *host_in, void *host_out, wsf
         }
     }
     cudaStream_t st = (cudaStream_t)stream;
+    if (p->can_pipeline_host()) {
+        const int rc = p->run_host_pipelined(host_in, host_out, st);
+        if (rc != WSFFT_SUCCESS) return rc;
+        return cuda_status(cudaStreamSynchronize(st));
+    }
     if (cudaMemcpyAsync(p->host_buf, host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return WSFFT_ERR_CUDA;
     int rc = p->run(p->host_buf, p->host_buf, st);

@@ -9,7 +9,7 @@ import torch
 import oracle
 from paper_2209_15040_gb300 import build
 from paper_2209_15040_gb300 import wsfft as W
-from tests._helpers import TOL, run_plan, seeded, to_device, to_host_c128
+from tests._helpers import DT, TOL, run_plan, seeded, to_device, to_host_c128
 
 pytestmark = pytest.mark.gpu
 
@@ -140,6 +140,31 @@ def test_execute_host_buffers():
     plan.execute_host(hin.data_ptr(), hout.data_ptr())
     ref = oracle.fftn(xc, rank=3)
     assert oracle.rel_l2(hout.numpy(), ref) < TOL["c32"]
+    plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["c32", "c16f", "c16bf"])
+@pytest.mark.parametrize("shape_full", [(1, 64, 32, 16), (3, 2, 128, 64), (1, 16, 8, 8), (1, 128, 128, 128)])
+@pytest.mark.parametrize("direction", [W.FORWARD, W.INVERSE])
+def test_execute_host_pipelined(dtype, shape_full, direction):
+    # rank-3 host-buffer executes overlap the copies with the supersteps in
+    # chunks (slab chunks in, inner-index chunks out); shapes cover fewer
+    # slabs than chunks, batches, and an inner size at the chunking limit
+    xs, xc = seeded(shape_full, 12, "normal" if dtype == "c32" else "uniform", dtype)
+    norm = W.NORM_PAPER if dtype == "c32" else W.NORM_ORTHO
+    plan = W.Plan(shape_full[1:], DT[dtype], direction, shape_full[0], norm)
+    hin = to_device(xs, dtype).cpu().pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for inplace in (False, True):
+        src = hin.clone().pin_memory() if inplace else hin
+        dst = src if inplace else hout
+        plan.execute_host(src.data_ptr(), dst.data_ptr())
+        got = to_host_c128(dst, dtype)
+        ref = oracle.fftn(xc, rank=3, sign=direction, norm=norm)
+        err = oracle.rel_l2(got, ref)
+        print(f"{shape_full} {dtype} dir={direction} inplace={inplace}: rel_l2={err:.3e}")
+        assert err < TOL[dtype], err
+    assert plan.sync_status() == W.SUCCESS
     plan.close()
 
 
