@@ -190,16 +190,21 @@ cudaError_t launch_tc_contig(int N, const void *in, void *out, const PassArgs &a
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
         // persistent: one resident block per SM, tiles strided by the grid
-        static int per_sm = 0, sms = 0;
-        if (per_sm == 0) {
-            int dev = 0;
-            if (cudaGetDevice(&dev) != cudaSuccess ||
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_contig512_kernel<S>, TC_THREADS,
-                                                              TC_SMEM) != cudaSuccess)
+        // (SM count and residency looked up once per device)
+        constexpr int kMaxDev = 64;
+        static int per_sm_dev[kMaxDev] = {}, sms_dev[kMaxDev] = {};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return cudaErrorInvalidValue;
+        if (per_sm_dev[dev] == 0) {
+            int ps = 0, n = 0;
+            if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, tc_contig512_kernel<S>, TC_THREADS, TC_SMEM) !=
+                    cudaSuccess)
                 return cudaErrorInvalidValue;
-            per_sm = per_sm > 1 ? 1 : per_sm;  // one block holds all 512 tensor-memory columns
+            sms_dev[dev] = n;
+            per_sm_dev[dev] = ps > 1 ? 1 : (ps < 1 ? -1 : ps);  // one block holds all 512 tensor-memory columns
         }
+        const int per_sm = per_sm_dev[dev], sms = sms_dev[dev];
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         const int64_t ntiles = (a.npencils + TC_P - 1) / TC_P;
         const int64_t blocks = std::min<int64_t>(ntiles, (int64_t)per_sm * sms);

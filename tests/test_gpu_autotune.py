@@ -64,3 +64,30 @@ def test_autotune_2d_without_cache(monkeypatch):
     ref = oracle.fftn(xs.astype(np.complex128), rank=2, sign=+1)
     assert oracle.rel_l2(y.cpu().numpy(), ref) < 5e-6
     plan.close()
+
+
+@pytest.mark.parametrize("dtype,code", [("c16f", W.C16F), ("c16bf", W.C16BF)])
+def test_autotune_half_storage_512(monkeypatch, dtype, code):
+    # the 16-bit candidates include the tensor-core contiguous superstep; the
+    # tuned plan must stay within the storage type's error bar either way
+    monkeypatch.delenv("WSFFT_TUNE_CACHE", raising=False)
+    shape = (8, 64, 512)
+    xs = inputs.complex_input(shape, 5, "uniform", dtype)
+    xc = inputs.storage_to_c128(xs, dtype)
+    if dtype == "c16f":
+        x = torch.from_numpy(np.ascontiguousarray(xs)).cuda()
+    else:
+        x = torch.from_numpy(np.ascontiguousarray(xs).view(np.int16)).view(torch.bfloat16).cuda()
+    y = torch.empty_like(x)
+    plan = W.Plan(shape, code, W.FORWARD, 1, W.NORM_ORTHO)
+    plan.autotune()
+    plan.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    assert plan.sync_status() == W.SUCCESS
+    got = y.cpu()
+    got = inputs.storage_to_c128(got.numpy() if dtype == "c16f" else got.view(torch.int16).numpy().view(np.uint16),
+                                 dtype)
+    ref = oracle.fftn(xc, rank=3, norm=W.NORM_ORTHO)
+    tol = 3e-3 if dtype == "c16f" else 2e-2
+    assert oracle.rel_l2(got, ref) < tol
+    plan.close()
