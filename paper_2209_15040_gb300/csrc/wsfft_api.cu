@@ -459,13 +459,18 @@ int Plan::build_schedule() {
                 p.E = 16;
                 p.tile = 8;
             }
-            if (p.N == 1024 && dtype == WSFFT_C32) {
+            if (p.N == 1024) {
                 // measured at 1024^3: 32 values per thread (radix 32 x 32, one
                 // exchange); contiguous: one warp per pencil, 8 per block;
-                // strided: 8 pencils per block at strides below 2^17 elements,
-                // 16 beyond (rows of 64 or 128 bytes)
+                // strided: 16 pencils per block at strides of 2^17 elements
+                // and more (128-byte rows), 8 below (16-bit storage there
+                // with 16 values per thread)
                 p.E = 32;
-                p.tile = p.kind == PASS_CONTIG ? 8 : (inner >= ((int64_t)1 << 17) ? 16 : 8);
+                p.tile = 8;
+                if (p.kind == PASS_STRIDED) {
+                    if (inner >= ((int64_t)1 << 17)) p.tile = 16;
+                    else if (dtype != WSFFT_C32) p.E = 16;
+                }
             }
             if (p.kind == PASS_STRIDED && p.N == 512 && inner % 16 == 0) {
                 // measured fastest at 512^3: complex64 with 32 values per
