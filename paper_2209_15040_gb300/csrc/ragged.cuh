@@ -114,46 +114,56 @@ template <class S>
 __device__ __forceinline__ void rag_tile(const RagArgs &a, const RagInst &I, int d, int tile,
                                          float2 *smem) {
     const int N = I.n[2 - d];
-    int lg = 0;
-    while ((1 << lg) < N) ++lg;
-    const float2 *tw = a.tw[lg - 1];
+    // stage tables by log2(N) - 1, with constant indices (a run-time index
+    // into the parameter array would copy it to local memory)
     if (d == 0) {
         switch (N) {
-            case 32: rag_contig<32, S>(I, tile, tw, a.ci, I.scale[0], smem); break;
-            case 64: rag_contig<64, S>(I, tile, tw, a.ci, I.scale[0], smem); break;
-            case 128: rag_contig<128, S>(I, tile, tw, a.ci, I.scale[0], smem); break;
-            default: rag_contig<256, S>(I, tile, tw, a.ci, I.scale[0], smem); break;
+            case 32: rag_contig<32, S>(I, tile, a.tw[4], a.ci, I.scale[0], smem); break;
+            case 64: rag_contig<64, S>(I, tile, a.tw[5], a.ci, I.scale[0], smem); break;
+            case 128: rag_contig<128, S>(I, tile, a.tw[6], a.ci, I.scale[0], smem); break;
+            default: rag_contig<256, S>(I, tile, a.tw[7], a.ci, I.scale[0], smem); break;
         }
     } else {
         const float sx = I.scale[d], sy = d == 2 ? a.co * I.scale[d] : I.scale[d];
         switch (N) {
-            case 32: rag_strided<32, S>(I, d, tile, tw, sx, sy, smem); break;
-            case 64: rag_strided<64, S>(I, d, tile, tw, sx, sy, smem); break;
-            case 128: rag_strided<128, S>(I, d, tile, tw, sx, sy, smem); break;
-            default: rag_strided<256, S>(I, d, tile, tw, sx, sy, smem); break;
+            case 32: rag_strided<32, S>(I, d, tile, a.tw[4], sx, sy, smem); break;
+            case 64: rag_strided<64, S>(I, d, tile, a.tw[5], sx, sy, smem); break;
+            case 128: rag_strided<128, S>(I, d, tile, a.tw[6], sx, sy, smem); break;
+            default: rag_strided<256, S>(I, d, tile, a.tw[7], sx, sy, smem); break;
         }
     }
 }
 
 template <class S>
-__global__ void __launch_bounds__(RAG_THREADS) ragged_kernel(RagArgs a) {
+__global__ void __launch_bounds__(RAG_THREADS, 4) ragged_kernel(RagArgs a) {
     __shared__ float2 smem[rag_smem_elems()];
     __shared__ int4 s_item;
     __shared__ RagInst s_inst;
     const int tid = threadIdx.x;
+    // Thread 0 keeps the queue one tile ahead: the next ticket and its item
+    // are fetched while the current tile is processed.
+    // Tickets are still processed in increasing order per block, so the
+    // smallest unfinished ticket is always some block's current tile and the
+    // waits stay deadlock-free.
+    int4 next = make_int4(ITEM_END, 0, 0, 0);
+    int after = 0;
+    auto fetch = [&](int ticket) {
+        next = make_int4(ITEM_END, 0, 0, 0);
+        if (ticket < a.nitems) {
+            const RagItem e = a.items[ticket];
+            next = make_int4(e.flags, e.inst, e.tile, 0);
+            after = (int)atomicAdd(&a.ctr[0], 1u);
+        }
+    };
+    if (tid == 0) fetch((int)atomicAdd(&a.ctr[0], 1u));
     for (;;) {
         if (tid == 0) {
-            const int ticket = (int)atomicAdd(&a.ctr[0], 1u);
-            int4 it = make_int4(ITEM_END, 0, 0, 0);
-            if (ticket < a.nitems) {
-                const RagItem e = a.items[ticket];
-                it = make_int4(e.flags, e.inst, e.tile, 0);
-            }
+            int4 it = next;
+            fetch(after);
             if (it.x & ITEM_WAIT) {
                 const int d = (it.x >> 8) & 3;  // wait for superstep d-1 of this instance
-                const RagInst &I = a.inst[it.y];
                 const uint32_t *dep = a.ctr + 1 + 2 * it.y + (d - 1);
-                const uint32_t target = (uint32_t)I.tiles[d - 1];
+                const uint32_t target = (uint32_t)a.inst[it.y].tiles[d - 1];
                 if (ld_acquire_u32(dep) < target) {
                     const uint64_t dl = gtimer() + a.timeout_ns;
                     while (ld_acquire_u32(dep) < target) {
@@ -173,10 +183,9 @@ __global__ void __launch_bounds__(RAG_THREADS) ragged_kernel(RagArgs a) {
         __syncthreads();
         const int4 it = s_item;
         if (it.x & ITEM_END) break;
-        if (!(it.x & ITEM_SKIP)) {
-            const RagInst I = s_inst;
-            rag_tile<S>(a, I, (it.x >> 8) & 3, it.z, smem);
-        }
+        // the instance record is read in place (shared memory, indexed by the
+        // superstep at run time; thread 0 rewrites it only after the barrier below)
+        if (!(it.x & ITEM_SKIP)) rag_tile<S>(a, s_inst, (it.x >> 8) & 3, it.z, smem);
         __syncthreads();
         if ((it.x & ITEM_SIGNAL) && !(it.x & ITEM_SKIP) && tid == 0) {
             __threadfence();
