@@ -262,6 +262,60 @@ def sizes_leg(W, dev, stream, hbm_peak, steps=20, warmup=3):
     return out
 
 
+def autograd_leg(W, dev, stream, steps=20, warmup=3):
+    """The differentiable configuration: batch 8 x 128^3 complex64 (N(0,1)),
+    loss = sum |W * FFT3(x)|^2 with W real uniform[0,1) of the same shape;
+    one step = forward (transform + loss) and backward (the hand-written
+    adjoint transform + torch's elementwise gradient of the loss), timed
+    with CUDA events.  Beside it: the forward and adjoint transforms alone."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(4)
+    shape = (8, 128, 128, 128)
+    x = torch.view_as_complex(torch.randn(shape + (2,), generator=g, device=dev)).contiguous()
+    x.requires_grad_(True)
+    w = torch.rand(shape, generator=g, device=dev)
+
+    def step():
+        x.grad = None
+        y = W.fftn(x, rank=3)
+        loss = (w * y).abs().square().sum()
+        loss.backward()
+        return loss
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_step = e0.elapsed_time(e1) / steps * 1e3
+    fwd = W.Plan((128, 128, 128), W.C32, W.FORWARD, 8)
+    adj = W.Plan((128, 128, 128), W.C32, W.INVERSE, 8, W.NORM_NONE)
+    y = torch.empty_like(x.detach())
+    xd = x.detach()
+    for _ in range(warmup):
+        fwd.execute(xd.data_ptr(), y.data_ptr(), stream)
+        adj.execute(y.data_ptr(), y.data_ptr(), stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fwd.execute(xd.data_ptr(), y.data_ptr(), stream)
+        adj.execute(y.data_ptr(), y.data_ptr(), stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_pair = e0.elapsed_time(e1) / steps * 1e3
+    fwd.close()
+    adj.close()
+    nbytes = 8 * 128 ** 3 * 8
+    return {"shape": list(shape), "dtype": "complex64", "us_per_step_fwd_bwd": round(t_step, 2),
+            "us_forward_plus_adjoint_transforms": round(t_pair, 2),
+            "transforms_gb_per_s_3pass": round(2 * 3 * 2 * nbytes / (t_pair * 1e-6) / 1e9, 1),
+            "note": "step includes torch's elementwise loss and its gradient; the 128 MiB batch sits in L2"}
+
+
 def ragged_leg(W, dev, stream, reps=5):
     """The ragged configuration (256 uneven 3D shapes from seed 4, N(0,1)):
     one persistent launch replayed from a captured CUDA graph vs one plan
@@ -409,6 +463,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch leg")
     ap.add_argument("--no-sizes", action="store_true", help="skip the other-sizes leg")
+    ap.add_argument("--no-autograd", action="store_true", help="skip the differentiable leg")
     ap.add_argument("--case", default=None,
                     help="profiling helper: run the default plan of shape D0,D1,D2 "
                          "--case-reps times (forward, N(0,1) input, storage --case-dtype) and exit")
@@ -541,6 +596,10 @@ def main():
     if not args.no_sizes and world == 1:
         sizes = sizes_leg(W, dev, stream, hbm_peak)
 
+    grad = None
+    if not args.no_autograd and world == 1:
+        grad = autograd_leg(W, dev, stream)
+
     ragged = None
     if not args.no_ragged:
         ragged = ragged_leg(W, dev, stream)
@@ -586,6 +645,8 @@ def main():
             line["ragged_batch"] = ragged
         if sizes:
             line["other_sizes"] = sizes
+        if grad:
+            line["autograd"] = grad
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
