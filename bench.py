@@ -219,13 +219,14 @@ def run_reference(args, world, rank):
 def sizes_leg(W, dev, stream, hbm_peak, steps=20, warmup=3):
     """The other transform sizes of the workload family, each timed like the
     main step ((FFT + IFFT)/2 per execute of the whole batch, data resident,
-    CUDA events on the stream):
-    cubes 128^3, 256^3 and 1024^3 (complex64 and float16 storage), 2D
+    CUDA events on the stream): cubes 32^3 (the small configuration:
+    latency-bound, three launches), 128^3, 256^3 and 1024^3 (complex64 and
+    float16 storage), 2D
     4096 x 4096 and 1D 2^20 x batch 512 (complex64).  GB/s counts one read and
     one write of the array per launch; the minimum-bytes fraction uses 2
     passes for 2D and 3D and 1 for 1D.  Arrays of 16 MiB (128^3) sit in L2:
     no roofline claim there."""
-    cases = [((128, 128, 128), 1, W.C32, 8), ((256, 256, 256), 1, W.C32, 8),
+    cases = [((32, 32, 32), 1, W.C32, 8), ((128, 128, 128), 1, W.C32, 8), ((256, 256, 256), 1, W.C32, 8),
              ((1024, 1024, 1024), 1, W.C32, 8), ((1024, 1024, 1024), 1, W.C16F, 4),
              ((4096, 4096), 1, W.C32, 8), ((1 << 20,), 512, W.C32, 8)]
     out = []
