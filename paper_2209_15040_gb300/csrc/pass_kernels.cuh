@@ -23,6 +23,16 @@
 
 namespace wsfft {
 
+// Programmatic dependent launch: every block lets the next kernel in the
+// stream start launching (its blocks take SM slots as this grid drains, and
+// its launch latency overlaps this grid's tail), and waits until the
+// previous kernel has completed and its writes are visible before touching
+// memory.  Both are no-ops for a launch without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Elements per thread for an axis of length N (the default variant).
 __host__ __device__ constexpr int default_E(int N) {
     return N <= 16 ? N : (N <= 64 ? 8 : (N == 512 ? 8 : 16));
@@ -123,6 +133,7 @@ template <int N, int E, int P, class S, bool TRANS, bool PLAIN = false>
 __global__ void __launch_bounds__(P *(N / E))
     contig_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
     extern __shared__ float2 smem[];
+    pdl_enter();
     constexpr int T = N / E;
     const int t = threadIdx.x % T;
     const int p = threadIdx.x / T;
@@ -231,6 +242,7 @@ template <int N, int E, int W, class S, bool TWID, bool PLAIN = false>
 __global__ void __launch_bounds__(W *(N / E), strided_min_blocks(W *(N / E), E))
     strided_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
     extern __shared__ float2 smem[];
+    pdl_enter();
     const int w = threadIdx.x % W;
     const int t = threadIdx.x / W;
     const int64_t q = ((int64_t)blockIdx.x + a.tile0) * W + w;
@@ -346,6 +358,7 @@ template <int N, int E, int W, class S, bool PLAIN = false>
 __global__ void __launch_bounds__((W / 2) * (N / E), strided_min_blocks((W / 2) * (N / E), 2 * E))
     strided_pair_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
     extern __shared__ float4 psmem[];
+    pdl_enter();
     using PT = typename Pair<S>::T;
     constexpr int WP = W / 2;
     const int wp = threadIdx.x % WP;
