@@ -14,8 +14,7 @@ template <int NC, int EC, int P, int NS, int ES, int W, class S>
 cudaError_t launch_eng(const EngArgs &a, int grid, cudaStream_t st) {
     using C = EngCfg<NC, EC, P, NS, ES, W, S>;
     auto kern = engine_kernel<NC, EC, P, NS, ES, W, S>;
-    static cudaError_t attr =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    const cudaError_t attr = set_smem_attr(reinterpret_cast<const void *>(kern), C::SMEM);
     if (attr != cudaSuccess) return attr;
     if (grid <= 0) return cudaSuccess;
     kern<<<grid, C::THREADS, C::SMEM, st>>>(a);
@@ -29,8 +28,7 @@ template <int NC, int EC, int P, int NS, int ES, int W, class S, int MODE, bool 
 cudaError_t launch_per_mode(const EngArgs &a, int *grid_per_sm, int grid, cudaStream_t st) {
     using C = PCfg<NC, EC, P, NS, ES, W, S, PAIRS>;
     auto kern = persist_kernel<NC, EC, P, NS, ES, W, S, MODE, PAIRS, (NC == 512 ? WSFFT_PERSIST_SUB : 1)>;
-    static cudaError_t attr =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    const cudaError_t attr = set_smem_attr(reinterpret_cast<const void *>(kern), C::SMEM);
     if (attr != cudaSuccess) return attr;
     if (grid_per_sm) {
         int nb = 0;
@@ -54,8 +52,7 @@ template <int N, class S>
 cudaError_t launch_wpp(const EngArgs &a, int *grid_per_sm, int grid, cudaStream_t st) {
     using C = WCfg<N, S>;
     auto kern = wp_persist_kernel<N, S>;
-    static cudaError_t attr =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    const cudaError_t attr = set_smem_attr(reinterpret_cast<const void *>(kern), C::SMEM);
     if (attr != cudaSuccess) return attr;
     if (grid_per_sm) {
         int nb = 0;
@@ -73,8 +70,7 @@ template <int N, class S>
 cudaError_t launch_wps(const WpStridedArgs &b, cudaStream_t st) {
     using C = WCfg<N, S>;
     auto kern = wp_strided_kernel<N, S>;
-    static cudaError_t attr =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    const cudaError_t attr = set_smem_attr(reinterpret_cast<const void *>(kern), C::SMEM);
     if (attr != cudaSuccess) return attr;
     if (b.inner % C::W != 0) return cudaErrorInvalidValue;
     const int64_t ntiles = b.npencils / C::W;

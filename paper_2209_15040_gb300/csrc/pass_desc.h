@@ -5,7 +5,29 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 namespace wsfft {
+
+// Dynamic shared memory above 48 KB must be enabled per kernel, and the
+// setting belongs to the current device: launchers call this before every
+// launch and it sets the attribute once per (kernel, device).
+inline cudaError_t set_smem_attr(const void *kernel, int bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(kernel, dev);
+    if (set.count(key)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) set[key] = bytes;
+    return e;
+}
 
 struct PassArgs {
     int64_t npencils;   // outer * inner pencils in this launch

@@ -17,8 +17,7 @@ namespace {
 
 template <class K>
 cudaError_t set_smem(K kernel, int bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return set_smem_attr(reinterpret_cast<const void *>(kernel), bytes);
 }
 
 inline bool plain_pass(const PassArgs &a) { return a.conj_in == 1.f && a.sx == 1.f && a.sy == 1.f; }
@@ -53,8 +52,8 @@ cudaError_t launch_contig(const void *in, void *out, const PassArgs &a, cudaStre
     constexpr int smem = contig_smem_elems(N, E, P, TRANS) * (int)sizeof(float2);
     const bool plain = !TRANS && plain_pass(a);
     auto kern = plain ? contig_kernel<N, E, P, S, TRANS, !TRANS> : contig_kernel<N, E, P, S, TRANS, false>;
-    static cudaError_t attr0 = set_smem(contig_kernel<N, E, P, S, TRANS, false>, smem);
-    static cudaError_t attr1 = set_smem(contig_kernel<N, E, P, S, TRANS, !TRANS>, smem);
+    const cudaError_t attr0 = set_smem(contig_kernel<N, E, P, S, TRANS, false>, smem);
+    const cudaError_t attr1 = set_smem(contig_kernel<N, E, P, S, TRANS, !TRANS>, smem);
     if (attr0 != cudaSuccess) return attr0;
     if (attr1 != cudaSuccess) return attr1;
     const int64_t blocks = (a.npencils + P - 1) / P;
@@ -70,7 +69,7 @@ cudaError_t launch_strided(const void *in, void *out, const PassArgs &a, cudaStr
     constexpr int smem = strided_smem_elems(N, E, W) * (int)sizeof(float2);
     // the general variant (conjugate on load, scale on store) even for plain
     // passes: measured faster than the multiply-free variant at 512^3
-    static cudaError_t attr = set_smem(strided_kernel<N, E, W, S, TWID, false>, smem);
+    const cudaError_t attr = set_smem(strided_kernel<N, E, W, S, TWID, false>, smem);
     if (attr != cudaSuccess) return attr;
     const int64_t blocks = (a.npencils + W - 1) / W;
     if (blocks <= 0) return cudaSuccess;
@@ -87,7 +86,7 @@ template <int N, int E, int W, class S>
 cudaError_t launch_strided_pair(const void *in, void *out, const PassArgs &a, cudaStream_t st) {
     constexpr int TH = (W / 2) * (N / E);
     constexpr int smem = N * (W / 2) * (int)sizeof(float4);
-    static cudaError_t attr = set_smem(strided_pair_kernel<N, E, W, S, false>, smem);
+    const cudaError_t attr = set_smem(strided_pair_kernel<N, E, W, S, false>, smem);
     if (attr != cudaSuccess) return attr;
     if (a.npencils % W != 0 || a.inner % W != 0) return cudaErrorInvalidValue;
     const int64_t blocks = a.npencils / W;
@@ -195,8 +194,7 @@ cudaError_t launch_tc_contig(int N, const void *in, void *out, const PassArgs &a
         return cudaErrorInvalidValue;
     } else {
         if (N != 512) return cudaErrorInvalidValue;
-        static cudaError_t attr = cudaFuncSetAttribute(tc_contig512_kernel<S>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        const cudaError_t attr = set_smem(tc_contig512_kernel<S>, TC_SMEM);
         if (attr != cudaSuccess) return attr;
         if (a.npencils <= 0) return cudaSuccess;
         const int64_t rows = a.npencils * 16;
