@@ -84,7 +84,7 @@ typedef enum {
     WSFFT_SUCCESS = 0,
     WSFFT_ERR_INVALID_ARG = -1,   /* null/misaligned pointer, bad enum, bad rank */
     WSFFT_ERR_INVALID_SIZE = -2,  /* non-power-of-two or out-of-range axis */
-    WSFFT_ERR_UNSUPPORTED = -3,   /* valid request this build does not handle */
+    WSFFT_ERR_UNSUPPORTED = -3,   /* valid request the library does not handle */
     WSFFT_ERR_ALLOC = -4,         /* device or host allocation failed */
     WSFFT_ERR_CUDA = -5,          /* a CUDA runtime call failed */
     WSFFT_ERR_DEVICE_TIMEOUT = -6 /* a bounded device-side wait ran out */

@@ -5,7 +5,7 @@
 // supports (one launch per superstep, and the two-trip persistent,
 // pipelined and warp-per-pencil schedules), then, for the fastest, each
 // one-launch pass in turn over the (values per thread, pencils per block)
-// shapes this build instantiates for its axis length.  Every candidate runs
+// shapes the library instantiates for its axis length.  Every candidate runs
 // on temporary buffers of the plan's size: two warm-up executes, then the
 // mean of three, timed with CUDA events on the caller's stream.
 //

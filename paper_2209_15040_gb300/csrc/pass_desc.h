@@ -71,7 +71,7 @@ enum PassKind {
 // Launch one superstep.  variant: contiguous -> transposed store,
 // strided -> four-step twiddle on store.  tile: 0 = the default tile shape
 // for (N, E); otherwise pencils per block (P or W) of an extra instantiated
-// shape.  Returns cudaErrorInvalidValue for a combination this build does
+// shape.  Returns cudaErrorInvalidValue for a combination the library does
 // not instantiate.
 cudaError_t launch_pass_c32(int kind, int N, int E, int tile, bool variant, const void *in,
                             void *out, const PassArgs &a, cudaStream_t st);
