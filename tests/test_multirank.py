@@ -1,0 +1,72 @@
+"""The N > 1 path of bench.py on CPU with gloo, world size 2: the rank
+helpers (process group, barrier, max over ranks) and the reference arm,
+which rank 0 alone runs and prints while the other ranks exit 0 without
+work.  No GPU is involved: every rank runs its own independent replica, so
+the only cross-rank traffic is the barrier and the timing reduction."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+_WORKER = r"""
+import os, sys
+sys.path.insert(0, {root!r})
+import bench
+world, rank, local = bench.dist_init()
+assert world == 2 and rank in (0, 1)
+bench.barrier(world)
+v = bench.allmax(world, 1.5 + rank)
+assert v == 2.5, v
+bench.barrier(world)
+import torch.distributed as dist
+dist.destroy_process_group()
+print("rank", rank, "ok", flush=True)
+"""
+
+
+def _env(port, rank):
+    env = dict(os.environ)
+    env.update({"WORLD_SIZE": "2", "RANK": str(rank), "LOCAL_RANK": str(rank),
+                "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "CUDA_VISIBLE_DEVICES": ""})
+    return env
+
+
+def test_rank_helpers_gloo_world_size_2():
+    port = _free_port()
+    code = _WORKER.format(root=ROOT)
+    procs = [subprocess.Popen([sys.executable, "-c", code], env=_env(port, r), cwd=ROOT,
+                              stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+             for r in range(2)]
+    outs = [p.communicate(timeout=120)[0] for p in procs]
+    for r, (p, out) in enumerate(zip(procs, outs)):
+        assert p.returncode == 0, out
+        assert f"rank {r} ok" in out
+
+
+def test_reference_arm_under_torchrun_world_size_2():
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
+           "--gpus", "2", "--steps", "1", "--warmup", "3"]
+    env = dict(os.environ)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout  # rank 0 alone prints
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
