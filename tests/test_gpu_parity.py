@@ -114,6 +114,30 @@ def test_1d_four_step(n):
     check((min(batch, 2), n), 1, seed=2, direction=W.INVERSE)
 
 
+def test_1d_2pow20_batch512_full_size():
+    # the 1D case of the 512^3 configuration at its full size (512 transforms
+    # of 2^20 points, 4 GiB, one workspace chunk): three batch entries against
+    # the oracle element by element, and Parseval over the whole batch
+    n, b = 1 << 20, 512
+    g = torch.Generator(device="cuda")
+    g.manual_seed(20)
+    x = torch.view_as_complex(torch.randn(b, n, 2, generator=g, device="cuda")).contiguous()
+    y = torch.empty_like(x)
+    plan = W.Plan((n,), W.C32, W.FORWARD, b)
+    plan.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    assert plan.sync_status() == W.SUCCESS
+    plan.close()
+    for i in (0, 257, 511):
+        xi = x[i].cpu().numpy().astype(np.complex128)
+        ref = oracle.fftn(xi, rank=1)
+        err = oracle.rel_l2(y[i].cpu().numpy(), ref)
+        assert err < TOL["c32"], (i, err)
+    ex = torch.linalg.vector_norm(x.view(torch.float32).double()) ** 2
+    ey = torch.linalg.vector_norm(y.view(torch.float32).double()) ** 2
+    assert abs(float(ey / (n * ex)) - 1.0) < 1e-5
+
+
 # -- reduced precision ---------------------------------------------------------
 
 @pytest.mark.parametrize("dtype", ["c16f", "c16bf"])
