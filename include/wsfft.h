@@ -34,7 +34,13 @@
  *    enqueued work completes.  in == out (in place) is allowed; otherwise in
  *    and out must not overlap.  `in` is never written when in != out.
  *  - Streams are cudaStream_t values passed as wsfft_stream (NULL = the legacy
- *    default stream).  Execute calls are asynchronous on that stream.
+ *    default stream).  Execute calls are asynchronous on that stream.  The
+ *    one-launch-per-superstep kernels of arrays up to 2 GiB are launched with
+ *    programmatic stream serialization and let the next kernel on the stream
+ *    begin launching early; work the caller enqueues afterwards is ordered
+ *    as usual, except a kernel the caller itself launches with that attribute,
+ *    which must wait for its predecessor (griddepcontrol.wait) before reading
+ *    the output.
  *  - Every function returns a wsfft_status.  No other error state is kept,
  *    except the per-plan device status word, which a device-side timeout
  *    sets; it is reported by wsfft_plan_sync_status.
