@@ -170,13 +170,15 @@ int wsfft_autotune(wsfft_plan plan, wsfft_stream stream);
  * plan: `values_per_thread` complex values per thread (the radix of the
  * register stages, 8, 16 or 32) and `tile` pencils per thread block; 0 and 0
  * restore the default.  Tile codes 1000 + W select the pencil-pair strided
- * kernel with W pencils per block; tile code 2000 selects the tensor-core
- * contiguous superstep (16-bit storage, N = 512; the values-per-thread
- * argument is then ignored).  Used by the autotuner.  Errors: INVALID_ARG,
- * UNSUPPORTED (that shape is not built for this pass).  A shape that needs
- * whole tiles (the pencil-pair kernel) on a pass whose pencil count or stride
- * is not a multiple of its tile makes wsfft_execute return CUDA without
- * launching. */
+ * kernel with W pencils per block, 3000 + W the same tile with the pair held
+ * in split form (real parts together, imaginary parts together) so that its
+ * butterflies run as packed FP32x2 instructions; tile code 2000 selects the
+ * tensor-core contiguous superstep (16-bit storage, N = 512; the
+ * values-per-thread argument is then ignored).  Used by the autotuner.
+ * Errors: INVALID_ARG, UNSUPPORTED (that shape is not built for this pass).
+ * A shape that needs whole tiles (either pencil-pair kernel) on a pass whose
+ * pencil count or stride is not a multiple of its tile makes wsfft_execute
+ * return CUDA without launching. */
 int wsfft_plan_set_pass_variant(wsfft_plan plan, int pass, int values_per_thread, int tile);
 
 /* Choose the schedule of a rank-3 transform n0 x n x n (n in {128, 256, 512,

@@ -130,13 +130,16 @@ double time_plan(Plan &p, const void *in, void *out, cudaStream_t st) {
 std::vector<std::pair<int, int>> shapes_for(int kind, int N, int dtype) {
     // tensor-core DFT-16 stage (16-bit storage only)
     if (kind == PASS_CONTIG && N == 512 && dtype != WSFFT_C32)
-        return {{32, 16}, {32, 8}, {32, 32}, {16, 8}, {8, 8}, {16, TC_TILE}};
+        return {{32, 16}, {32, 8}, {32, 32}, {16, 8}, {8, 8}, {16, TC_TILE}, {16, SPLIT_TILE + 8},
+                {16, SPLIT_TILE + 16}, {8, SPLIT_TILE + 8}};
     if (kind == PASS_STRIDED && N == 512)
         return {{32, 16}, {32, 8},  {32, 32}, {16, 16}, {8, 8}, {16, 8}, {16, 32}, {8, PAIR_TILE + 16},
-                {8, PAIR_TILE + 32}, {8, PAIR_TILE + 8}, {16, PAIR_TILE + 16}, {16, PAIR_TILE + 32}};
+                {8, PAIR_TILE + 32}, {8, PAIR_TILE + 8}, {16, PAIR_TILE + 16}, {16, PAIR_TILE + 32},
+                {16, SPLIT_TILE + 16}, {16, SPLIT_TILE + 32}, {8, SPLIT_TILE + 16}, {8, SPLIT_TILE + 32}};
     if (kind == PASS_STRIDED && N == 256) return {{16, 32}, {8, 16}, {8, PAIR_TILE + 16}};
     if (kind == PASS_STRIDED && N == 1024) return {{16, 8}};
-    if (kind == PASS_CONTIG && N == 512) return {{32, 16}, {32, 8}, {32, 32}, {16, 8}, {8, 8}};
+    if (kind == PASS_CONTIG && N == 512)
+        return {{32, 16}, {32, 8}, {32, 32}, {16, 8}, {8, 8}, {16, SPLIT_TILE + 8}, {16, SPLIT_TILE + 16}};
     if (kind == PASS_CONTIG && N == 256) return {{8, 8}};
     return {};
 }

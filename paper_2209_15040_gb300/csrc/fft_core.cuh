@@ -119,6 +119,72 @@ __device__ __forceinline__ float4 rot16(float4 a) {
     return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
+// The same element of two adjacent pencils in split form: pencil 0 is
+// (re.x, im.x), pencil 1 is (re.y, im.y).  Each real operation of the
+// one-pencil butterfly becomes one packed FP32x2 instruction on the pair
+// (sm_100 and later), with the same rounding in each lane, so the pair costs
+// the instruction issue of a single pencil.
+struct cpair {
+    float2 re, im;
+};
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 f2dup(float v) { return make_float2(v, v); }
+__device__ __forceinline__ cpair cadd(cpair a, cpair b) {
+    return {__fadd2_rn(a.re, b.re), __fadd2_rn(a.im, b.im)};
+}
+__device__ __forceinline__ cpair csub(cpair a, cpair b) {
+    return {__fadd2_rn(a.re, f2neg(b.re)), __fadd2_rn(a.im, f2neg(b.im))};
+}
+// one twiddle for both pencils; per lane exactly the float2 cmul above
+__device__ __forceinline__ cpair cmul(cpair a, float2 w) {
+    const float2 wr = f2dup(w.x), wi = f2dup(w.y);
+    return {__ffma2_rn(a.re, wr, f2neg(__fmul2_rn(a.im, wi))), __ffma2_rn(a.re, wi, __fmul2_rn(a.im, wr))};
+}
+
+// rot16 on a split pair: per lane the same operations as the float2 version
+template <int J>
+__device__ __forceinline__ cpair rot16(cpair a) {
+    constexpr int j = ((J % 16) + 16) % 16;
+    constexpr float H = 0.70710678118654752440f;   // cos(pi/4)
+    constexpr float C1 = 0.92387953251128675613f;  // cos(pi/8)
+    constexpr float S1 = 0.38268343236508977173f;  // sin(pi/8)
+    const float2 h = f2dup(H);
+    if constexpr (j == 0) {
+        return a;
+    } else if constexpr (j == 4) {
+        return {a.im, f2neg(a.re)};
+    } else if constexpr (j == 8) {
+        return {f2neg(a.re), f2neg(a.im)};
+    } else if constexpr (j == 12) {
+        return {f2neg(a.im), a.re};
+    } else if constexpr (j == 2) {
+        return {__fmul2_rn(__fadd2_rn(a.re, a.im), h), __fmul2_rn(__fadd2_rn(a.im, f2neg(a.re)), h)};
+    } else if constexpr (j == 6) {
+        return {__fmul2_rn(__fadd2_rn(a.im, f2neg(a.re)), h), f2neg(__fmul2_rn(__fadd2_rn(a.re, a.im), h))};
+    } else if constexpr (j == 10) {
+        return {f2neg(__fmul2_rn(__fadd2_rn(a.re, a.im), h)), __fmul2_rn(__fadd2_rn(a.re, f2neg(a.im)), h)};
+    } else if constexpr (j == 14) {
+        return {__fmul2_rn(__fadd2_rn(a.re, f2neg(a.im)), h), __fmul2_rn(__fadd2_rn(a.re, a.im), h)};
+    } else {
+        constexpr float c = (j == 1) ? C1 : (j == 3) ? S1 : (j == 5) ? -S1 : (j == 7) ? -C1
+                          : (j == 9) ? -C1 : (j == 11) ? -S1 : (j == 13) ? S1 : C1;
+        constexpr float s = (j == 1) ? S1 : (j == 3) ? C1 : (j == 5) ? C1 : (j == 7) ? S1
+                          : (j == 9) ? -S1 : (j == 11) ? -C1 : (j == 13) ? -C1 : -S1;
+        const float2 cc = f2dup(c), ss = f2dup(s);
+        return {__ffma2_rn(a.re, cc, __fmul2_rn(a.im, ss)), __ffma2_rn(a.im, cc, f2neg(__fmul2_rn(a.re, ss)))};
+    }
+}
+template <int J>
+__device__ __forceinline__ cpair rot32(cpair a) {
+    constexpr int j = ((J % 32) + 32) % 32;
+    if constexpr (j % 2 == 0) {
+        return rot16<j / 2>(a);
+    } else {
+        const float2 cc = f2dup((float)cos_pi16(j)), ss = f2dup((float)cos_pi16(8 - j));
+        return {__ffma2_rn(a.re, cc, __fmul2_rn(a.im, ss)), __ffma2_rn(a.im, cc, f2neg(__fmul2_rn(a.re, ss)))};
+    }
+}
+
 // In-register R-point forward DFT (R in {1,2,4,8,16,32}), natural order in and
 // out: split into even and odd halves, transform each, combine with
 // exp(-2*pi*i*k/R).

@@ -44,6 +44,7 @@ struct PassArgs {
     int64_t tile0;      // strided launches: index of the first tile (set by the launcher)
     int *status;        // plan's device status word (kernels with bounded waits)
     uint64_t timeout_ns;  // bound of each wait
+    int no_pdl;         // 1: launch without programmatic dependent launch
 };
 
 // tile codes at or above this select the complex64 pencil-pair strided
@@ -57,6 +58,9 @@ constexpr int TC_TILE = 2000;
 //   [256, 768)  w512^(k1*n2) at 256 + n2*16 + k1 (k1 in [0,16), n2 in [0,32))
 constexpr int TC_TABLE_TW = 256;
 constexpr int TC_TABLE_FLOAT2 = 768;
+// tile codes at or above this select the split-form pencil-pair strided
+// kernel (packed FP32x2 butterflies) with (code - SPLIT_TILE) pencils per block
+constexpr int SPLIT_TILE = 3000;
 
 enum PassKind {
     PASS_CONTIG = 0,     // one launch, contiguous axis

@@ -18,6 +18,8 @@
 //    index, which keeps shared-memory exchanges free of bank conflicts.
 #pragma once
 
+#include <type_traits>
+
 #include "fft_core.cuh"
 #include "pass_desc.h"
 
@@ -354,7 +356,204 @@ struct StridedPairAcc {
     __device__ __forceinline__ void after_load() const {}
 };
 
-template <int N, int E, int W, class S, bool PLAIN = false>
+// Split-form pencil pairs: the same tile and memory accesses as the pairs
+// above, but each value is held as (re0, re1), (im0, im1) so that the
+// butterflies run as packed FP32x2 instructions (cpair).  16-bit storage
+// converts straight into that form (two byte permutes per element pair).
+template <class S>
+struct SplitPair;
+template <>
+struct SplitPair<float2> {
+    using T = float4;
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static cpair load(const T *p) {
+        const float4 v = ld_op<OP>(p);
+        return {make_float2(v.x, v.z), make_float2(v.y, v.w)};
+    }
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static void store(T *p, cpair v) {
+        st_op<OP>(p, make_float4(v.re.x, v.im.x, v.re.y, v.im.y));
+    }
+};
+template <>
+struct SplitPair<__half2> {
+    using T = uint2;
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static cpair load(const T *p) {
+        const uint2 u = ld_op<OP>(p);
+        const __half2 a = *reinterpret_cast<const __half2 *>(&u.x);  // (re0, im0)
+        const __half2 b = *reinterpret_cast<const __half2 *>(&u.y);  // (re1, im1)
+        return {__half22float2(__lows2half2(a, b)), __half22float2(__highs2half2(a, b))};
+    }
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static void store(T *p, cpair v) {
+        const __half2 r = __float22half2_rn(v.re), i = __float22half2_rn(v.im);
+        const __half2 a = __lows2half2(r, i), b = __highs2half2(r, i);
+        uint2 u;
+        u.x = *reinterpret_cast<const unsigned *>(&a);
+        u.y = *reinterpret_cast<const unsigned *>(&b);
+        st_op<OP>(p, u);
+    }
+};
+template <>
+struct SplitPair<__nv_bfloat162> {
+    using T = uint2;
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static cpair load(const T *p) {
+        const uint2 u = ld_op<OP>(p);
+        const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&u.x);
+        const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
+        return {__bfloat1622float2(__lows2bfloat162(a, b)), __bfloat1622float2(__highs2bfloat162(a, b))};
+    }
+    template <int OP = OP_DEF>
+    __device__ __forceinline__ static void store(T *p, cpair v) {
+        const __nv_bfloat162 r = __float22bfloat162_rn(v.re), i = __float22bfloat162_rn(v.im);
+        const __nv_bfloat162 a = __lows2bfloat162(r, i), b = __highs2bfloat162(r, i);
+        uint2 u;
+        u.x = *reinterpret_cast<const unsigned *>(&a);
+        u.y = *reinterpret_cast<const unsigned *>(&b);
+        st_op<OP>(p, u);
+    }
+};
+
+template <class S, int W, bool PLAIN>
+struct StridedSplitAcc {
+    using value_type = cpair;
+    using PT = typename SplitPair<S>::T;
+    const PT *in;       // this pair's element 0
+    PT *out;
+    float4 *sm;         // tile base, [k][W/2] float4 (re0, re1, im0, im1)
+    int64_t stride;     // in pair units: element stride / 2
+    int wp;
+    float ci, sx, sy;
+    bool active;
+    __device__ __forceinline__ cpair gload(int k) const {
+        cpair v = active ? SplitPair<S>::load(in + (int64_t)k * stride)
+                         : cpair{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if constexpr (!PLAIN) v.im = __fmul2_rn(v.im, f2dup(ci));
+        return v;
+    }
+    __device__ __forceinline__ void gstore(int k, cpair v) const {
+        if constexpr (!PLAIN) {
+            v.re = __fmul2_rn(v.re, f2dup(sx));
+            v.im = __fmul2_rn(v.im, f2dup(sy));
+        }
+        if (active) SplitPair<S>::store(out + (int64_t)k * stride, v);
+    }
+    __device__ __forceinline__ int sidx(int k) const { return k * (W / 2) + wp; }
+    __device__ __forceinline__ void sstore(int k, cpair v) const {
+        sm[sidx(k)] = make_float4(v.re.x, v.re.y, v.im.x, v.im.y);
+    }
+    __device__ __forceinline__ cpair sload(int k) const {
+        const float4 v = sm[sidx(k)];
+        return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ void after_load() const {}
+};
+
+// Split form of two single elements (one of each pencil of a pair)
+template <class S>
+struct SplitCvt;
+template <>
+struct SplitCvt<float2> {
+    __device__ __forceinline__ static float2 zero() { return make_float2(0.f, 0.f); }
+    __device__ __forceinline__ static cpair join(float2 a, float2 b) {
+        return {make_float2(a.x, b.x), make_float2(a.y, b.y)};
+    }
+    __device__ __forceinline__ static void split(cpair v, float2 &a, float2 &b) {
+        a = make_float2(v.re.x, v.im.x);
+        b = make_float2(v.re.y, v.im.y);
+    }
+};
+template <>
+struct SplitCvt<__half2> {
+    __device__ __forceinline__ static __half2 zero() { return __float2half2_rn(0.f); }
+    __device__ __forceinline__ static cpair join(__half2 a, __half2 b) {
+        return {__half22float2(__lows2half2(a, b)), __half22float2(__highs2half2(a, b))};
+    }
+    __device__ __forceinline__ static void split(cpair v, __half2 &a, __half2 &b) {
+        const __half2 r = __float22half2_rn(v.re), i = __float22half2_rn(v.im);
+        a = __lows2half2(r, i);
+        b = __highs2half2(r, i);
+    }
+};
+template <>
+struct SplitCvt<__nv_bfloat162> {
+    __device__ __forceinline__ static __nv_bfloat162 zero() { return __float2bfloat162_rn(0.f); }
+    __device__ __forceinline__ static cpair join(__nv_bfloat162 a, __nv_bfloat162 b) {
+        return {__bfloat1622float2(__lows2bfloat162(a, b)), __bfloat1622float2(__highs2bfloat162(a, b))};
+    }
+    __device__ __forceinline__ static void split(cpair v, __nv_bfloat162 &a, __nv_bfloat162 &b) {
+        const __nv_bfloat162 r = __float22bfloat162_rn(v.re), i = __float22bfloat162_rn(v.im);
+        a = __lows2bfloat162(r, i);
+        b = __highs2bfloat162(r, i);
+    }
+};
+
+// Contiguous axis, split-form pencil pairs: the T = N/E threads of a pair
+// carry element k of two neighbouring pencils (q, q+1) as one cpair.  Each
+// global access is one pencil's element (so a warp still reads consecutive
+// addresses of one pencil per instruction), each shared access 16 bytes.
+template <class S, bool PLAIN, bool WARP>
+struct ContigSplitAcc {
+    using value_type = cpair;
+    const S *in;   // pencil q's first element; pencil q+1 follows at +N
+    S *out;
+    float4 *sm;    // this pair's shared-memory row, float4 (re0, re1, im0, im1)
+    int n;         // pencil length
+    float ci, sx, sy;
+    bool act0, act1;
+    __device__ __forceinline__ cpair gload(int k) const {
+        const S a = act0 ? in[k] : SplitCvt<S>::zero();
+        const S b = act1 ? in[n + k] : SplitCvt<S>::zero();
+        cpair v = SplitCvt<S>::join(a, b);
+        if constexpr (!PLAIN) v.im = __fmul2_rn(v.im, f2dup(ci));
+        return v;
+    }
+    __device__ __forceinline__ void gstore(int k, cpair v) const {
+        if constexpr (!PLAIN) {
+            v.re = __fmul2_rn(v.re, f2dup(sx));
+            v.im = __fmul2_rn(v.im, f2dup(sy));
+        }
+        S a, b;
+        SplitCvt<S>::split(v, a, b);
+        if (act0) out[k] = a;
+        if (act1) out[n + k] = b;
+    }
+    // same padding as the one-pencil rows: one pad per 16 elements
+    __device__ __forceinline__ static int sidx(int k) { return (int)((unsigned)k + ((unsigned)k >> 4)); }
+    __device__ __forceinline__ void sstore(int k, cpair v) const {
+        sm[sidx(k)] = make_float4(v.re.x, v.re.y, v.im.x, v.im.y);
+    }
+    __device__ __forceinline__ cpair sload(int k) const {
+        const float4 v = sm[sidx(k)];
+        return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    }
+    __device__ __forceinline__ void sync() const {
+        if constexpr (WARP) __syncwarp();
+        else __syncthreads();
+    }
+    __device__ __forceinline__ void after_load() const {}
+};
+
+// P pencils per block as P/2 split-form pairs
+template <int N, int E, int P, class S, bool PLAIN>
+__global__ void __launch_bounds__((P / 2) * (N / E))
+    contig_split_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
+    extern __shared__ float4 qsmem[];
+    pdl_enter();
+    constexpr int T = N / E;
+    const int t = threadIdx.x % T;
+    const int pp = threadIdx.x / T;
+    const int64_t q = (int64_t)blockIdx.x * P + 2 * pp;
+    ContigSplitAcc<S, PLAIN, (T <= 32)> acc{in + q * N, out + q * N, qsmem + pp * contig_PS(N), N,
+                                            a.conj_in, a.sx, a.sy, q < a.npencils, q + 1 < a.npencils};
+    pencil_fft<N, E>(acc, t, a.tw);
+}
+
+// SPLIT selects the split-form accessor (packed FP32x2 butterflies)
+template <int N, int E, int W, class S, bool PLAIN = false, bool SPLIT = false>
 __global__ void __launch_bounds__((W / 2) * (N / E), strided_min_blocks((W / 2) * (N / E), 2 * E))
     strided_pair_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
     extern __shared__ float4 psmem[];
@@ -367,7 +566,7 @@ __global__ void __launch_bounds__((W / 2) * (N / E), strided_min_blocks((W / 2) 
     const int64_t o = q >> a.log_inner;
     const int64_t i = q & (a.inner - 1);
     const int64_t base = o * ((int64_t)N << a.log_inner) + i;   // element offset (even)
-    StridedPairAcc<S, W, PLAIN> acc;
+    std::conditional_t<SPLIT, StridedSplitAcc<S, W, PLAIN>, StridedPairAcc<S, W, PLAIN>> acc;
     acc.in = reinterpret_cast<const PT *>(in + base);
     acc.out = reinterpret_cast<PT *>(out + base);
     acc.sm = psmem;

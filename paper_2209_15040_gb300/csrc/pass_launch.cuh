@@ -28,7 +28,7 @@ inline bool plain_pass(const PassArgs &a) { return a.conj_in == 1.f && a.sx == 1
 // and 5% at 256^3, but 14% slower at 1024^3 (8 GiB), so larger passes
 // launch plainly.
 inline bool pdl_pass(const PassArgs &a, int N, int elem_bytes) {
-    return a.npencils * (int64_t)N * elem_bytes <= ((int64_t)2 << 30);
+    return !a.no_pdl && a.npencils * (int64_t)N * elem_bytes <= ((int64_t)2 << 30);
 }
 template <class... KArgs, class... Args>
 cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), unsigned grid, unsigned block, int smem,
@@ -63,6 +63,23 @@ cudaError_t launch_contig(const void *in, void *out, const PassArgs &a, cudaStre
                       a);
 }
 
+template <int N, int E, int P, class S>
+cudaError_t launch_contig_split(const void *in, void *out, const PassArgs &a, cudaStream_t st) {
+    static_assert(P % 2 == 0, "pairs");
+    constexpr int smem = (P / 2) * contig_PS(N) * (int)sizeof(float4);
+    const bool plain = plain_pass(a);
+    auto kern = plain ? contig_split_kernel<N, E, P, S, true> : contig_split_kernel<N, E, P, S, false>;
+    const cudaError_t attr0 = set_smem(contig_split_kernel<N, E, P, S, false>, smem);
+    const cudaError_t attr1 = set_smem(contig_split_kernel<N, E, P, S, true>, smem);
+    if (attr0 != cudaSuccess) return attr0;
+    if (attr1 != cudaSuccess) return attr1;
+    const int64_t blocks = (a.npencils + P - 1) / P;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    return launch_pdl(pdl_pass(a, N, sizeof(S)), kern, (unsigned)blocks, (P / 2) * (N / E), smem, st,
+                      (const S *)in, (S *)out, a);
+}
+
 template <int N, int E, int W, class S, bool TWID>
 cudaError_t launch_strided(const void *in, void *out, const PassArgs &a, cudaStream_t st) {
     constexpr int T = N / E;
@@ -82,11 +99,11 @@ cudaError_t launch_strided(const void *in, void *out, const PassArgs &a, cudaStr
 
 // Pencil-pair strided kernel: tile codes >= PAIR_TILE select it with
 // W = tile - PAIR_TILE pencils per block.
-template <int N, int E, int W, class S>
+template <int N, int E, int W, class S, bool SPLIT = false>
 cudaError_t launch_strided_pair(const void *in, void *out, const PassArgs &a, cudaStream_t st) {
     constexpr int TH = (W / 2) * (N / E);
     constexpr int smem = N * (W / 2) * (int)sizeof(float4);
-    const cudaError_t attr = set_smem(strided_pair_kernel<N, E, W, S, false>, smem);
+    const cudaError_t attr = set_smem(strided_pair_kernel<N, E, W, S, false, SPLIT>, smem);
     if (attr != cudaSuccess) return attr;
     if (a.npencils % W != 0 || a.inner % W != 0) return cudaErrorInvalidValue;
     const int64_t blocks = a.npencils / W;
@@ -97,7 +114,7 @@ cudaError_t launch_strided_pair(const void *in, void *out, const PassArgs &a, cu
     // The general variant (conjugate on load, scale on store) is used even
     // for plain passes: at 512^3 it measured 8% faster than the variant
     // without those multiplies.
-    return launch_pdl(pdl_pass(a, N, sizeof(S)), strided_pair_kernel<N, E, W, S, false>, (unsigned)blocks, TH, smem,
+    return launch_pdl(pdl_pass(a, N, sizeof(S)), strided_pair_kernel<N, E, W, S, false, SPLIT>, (unsigned)blocks, TH, smem,
                       st, (const S *)in, (S *)out, b);
 }
 
@@ -143,6 +160,23 @@ cudaError_t launch_extra(int kind, int N, int E, int tile, const void *in, void 
     WSFFT_XC(512, 32, 32)
     WSFFT_XC(512, 8, 8)
     WSFFT_XC(256, 8, 8)
+    if (kind == PASS_CONTIG && tile >= SPLIT_TILE) {
+        if (N == 512 && E == 16 && tile == SPLIT_TILE + 16) return launch_contig_split<512, 16, 16, S>(in, out, a, st);
+        if (N == 512 && E == 16 && tile == SPLIT_TILE + 8) return launch_contig_split<512, 16, 8, S>(in, out, a, st);
+        if (N == 512 && E == 8 && tile == SPLIT_TILE + 8) return launch_contig_split<512, 8, 8, S>(in, out, a, st);
+        return cudaErrorInvalidValue;
+    }
+    if (kind == PASS_STRIDED && tile >= SPLIT_TILE) {
+        if (N == 512 && E == 16 && tile == SPLIT_TILE + 16)
+            return launch_strided_pair<512, 16, 16, S, true>(in, out, a, st);
+        if (N == 512 && E == 16 && tile == SPLIT_TILE + 32)
+            return launch_strided_pair<512, 16, 32, S, true>(in, out, a, st);
+        if (N == 512 && E == 8 && tile == SPLIT_TILE + 16)
+            return launch_strided_pair<512, 8, 16, S, true>(in, out, a, st);
+        if (N == 512 && E == 8 && tile == SPLIT_TILE + 32)
+            return launch_strided_pair<512, 8, 32, S, true>(in, out, a, st);
+        return cudaErrorInvalidValue;
+    }
     if (kind == PASS_STRIDED && tile >= PAIR_TILE) {
         if (N == 512 && E == 8 && tile == PAIR_TILE + 16) return launch_strided_pair<512, 8, 16, S>(in, out, a, st);
         if (N == 512 && E == 8 && tile == PAIR_TILE + 32) return launch_strided_pair<512, 8, 32, S>(in, out, a, st);

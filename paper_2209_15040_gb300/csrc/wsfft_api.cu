@@ -335,11 +335,12 @@ int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
     } else {
         // x: one launch of the strided superstep kernel, with the shape of
         // the one-launch-per-superstep schedule at 512 (16 pencils per block:
-        // 32 values per thread in complex64, pencil pairs in the 16-bit types)
+        // 32 values per thread in complex64, split-form pencil pairs in the
+        // 16-bit types)
         b.kind = PASS_STRIDED;
         b.N = (int)n0;
-        b.E = n0 == 512 ? (dtype == WSFFT_C32 ? 32 : 8) : default_E((int)n0);
-        b.tile = n0 == 512 ? (dtype == WSFFT_C32 ? 16 : PAIR_TILE + 16) : 0;
+        b.E = n0 == 512 ? (dtype == WSFFT_C32 ? 32 : 16) : default_E((int)n0);
+        b.tile = n0 == 512 ? (dtype == WSFFT_C32 ? 16 : SPLIT_TILE + 16) : 0;
         b.inner = n * n;
         b.npencils_per_batch = n * n;
         b.src = SRC_OUT;
@@ -453,11 +454,14 @@ int Plan::build_schedule() {
             p.variant = false;
             if (p.kind == PASS_CONTIG && p.N == 512) {
                 // measured fastest at 512^3: 16 values per thread (radices
-                // 16, 16, 2), 8 pencils per 256-thread block (32 values per
-                // thread matched it forward but lost 30% with the conjugate
-                // on load of the inverse)
+                // 16, 16, 2), 8 pencils per block (32 values per thread
+                // matched it forward but lost 30% with the conjugate on load
+                // of the inverse); complex64 one pencil per warp (256-thread
+                // blocks, at the copy bandwidth), the 16-bit types as
+                // split-form pairs (one pair per warp, packed FP32x2
+                // butterflies: 13% faster there, the same in complex64)
                 p.E = 16;
-                p.tile = 8;
+                p.tile = dtype == WSFFT_C32 ? 8 : SPLIT_TILE + 8;
             }
             if (p.N == 1024) {
                 // measured at 1024^3: 32 values per thread (radix 32 x 32, one
@@ -473,12 +477,17 @@ int Plan::build_schedule() {
                 }
             }
             if (p.kind == PASS_STRIDED && p.N == 512 && inner % 16 == 0) {
-                // measured fastest at 512^3: complex64 with 32 values per
-                // thread and 16 pencils per block (one shared-memory exchange);
-                // the 16-bit types with pencil pairs (two adjacent elements per
-                // access), 8 values per pencil, 16 pencils per block
-                p.E = dtype == WSFFT_C32 ? 32 : 8;
-                p.tile = dtype == WSFFT_C32 ? 16 : PAIR_TILE + 16;
+                // measured fastest at 512^3: split-form pencil pairs (packed
+                // FP32x2 butterflies, two adjacent elements per access), 16
+                // values per pencil, 16 pencils per block, except for complex64
+                // at strides of 2^17 elements and more, where 32 values per
+                // thread for one pencil (one shared-memory exchange) match them
+                p.E = 16;
+                p.tile = SPLIT_TILE + 16;
+                if (dtype == WSFFT_C32 && inner >= ((int64_t)1 << 17)) {
+                    p.E = 32;
+                    p.tile = 16;
+                }
             }
             p.inner = inner;
             p.npencils_per_batch = total / d[ax];
@@ -509,6 +518,11 @@ int Plan::build_schedule() {
             passes[kv.first].tile = kv.second.second;
         }
     }
+    // a launch right after a split-form contiguous launch goes without
+    // programmatic dependent launch: its early blocks slowed that kernel's
+    // tail (512^3 FP16: 0.752 ms per transform with it, 0.717 ms without)
+    for (size_t i = 0; i < passes.size(); ++i)
+        passes[i].no_pdl = i > 0 && passes[i - 1].kind == PASS_CONTIG && passes[i - 1].tile >= SPLIT_TILE;
     for (auto &p : passes) {
         if (p.N > 4096 || !is_pow2(p.N)) return WSFFT_ERR_INVALID_SIZE;
         p.tw = p.tile == TC_TILE ? tc_table(p.N) : table(p.N, p.E);
@@ -629,6 +643,7 @@ PassArgs Plan::pass_args(const PassSpec &p, int64_t npencils) const {
     a.tw_mask = p.twid_len ? (int)(p.twid_len - 1) : 0;
     a.status = d_status;
     a.timeout_ns = (uint64_t)wait_timeout_ns;
+    a.no_pdl = p.no_pdl ? 1 : 0;
     return a;
 }
 
@@ -986,7 +1001,6 @@ int wsfft_plan_create_ragged(wsfft_plan *plan, int count, const int64_t *dims, i
         return fail(WSFFT_ERR_ALLOC);
     }
     cudaMemset(p->d_status, 0, sizeof(int));
-    const bool inv = direction == WSFFT_INVERSE;
     std::vector<RagInst> inst((size_t)count);
     for (int i = 0; i < count; ++i) {
         RagInst &I = inst[i];

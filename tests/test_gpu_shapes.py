@@ -1,7 +1,8 @@
 """GPU parity of every kernel shape the library instantiates besides the
 defaults: each (values per thread, pencils per block) shape of the
 contiguous-axis and strided-axis superstep kernels, including the
-pencil-pair and the 32-values-per-thread (radix-32) shapes, selected with
+pencil-pair, split-form pencil-pair and the 32-values-per-thread (radix-32)
+shapes, selected with
 wsfft_plan_set_pass_variant and compared with the FP64 oracle, for every
 storage type, on full tiles and on ragged tails (pencil counts that are not a
 multiple of the tile)."""
@@ -18,6 +19,7 @@ pytestmark = pytest.mark.gpu
 
 PAIR = 1000  # tile codes from PAIR_TILE on select the pencil-pair kernel
 TC = 2000    # tile code of the tensor-core contiguous superstep (16-bit storage, 512)
+SPLIT = 3000  # tile codes from SPLIT_TILE on select the split-form (packed FP32x2) pair kernel
 
 # (values per thread, tile) shapes per axis length
 CONTIG = {512: [(32, 16), (32, 8), (32, 32), (16, 8), (8, 8)], 256: [(8, 8)], 1024: [(32, 8)]}
@@ -25,6 +27,8 @@ STRIDED = {512: [(32, 16), (32, 8), (32, 32), (16, 16), (8, 8), (16, 8), (16, 32
            256: [(16, 32), (8, 16)], 1024: [(16, 8), (32, 8), (32, 16)]}
 PAIRS = {512: [(8, PAIR + 16), (8, PAIR + 32), (8, PAIR + 8), (16, PAIR + 16), (16, PAIR + 32)],
          256: [(8, PAIR + 16)]}
+SPLITS = {512: [(16, SPLIT + 16), (16, SPLIT + 32), (8, SPLIT + 16), (8, SPLIT + 32)]}
+CONTIG_SPLITS = {512: [(16, SPLIT + 16), (16, SPLIT + 8), (8, SPLIT + 8)]}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -69,21 +73,22 @@ DTYPES = ["c32", "c16f", "c16bf"]
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("shape", CONTIG[512])
+@pytest.mark.parametrize("shape", CONTIG[512] + CONTIG_SPLITS[512])
 def test_contig_512(dtype, shape):
     # pass 0 is the contiguous superstep of length 512 (8*512 = 4096 pencils)
     run_variant((64, 8, 512), 3, dtype, [(0, *shape)])
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("shape", CONTIG[512])
+@pytest.mark.parametrize("shape", CONTIG[512] + CONTIG_SPLITS[512])
 def test_contig_512_ragged(dtype, shape):
-    # 37 pencils: the last tile of every shape is partial
+    # 37 pencils: the last tile of every shape is partial (and, for the
+    # split-form pairs, the last pair has one pencil)
     run_variant((37, 512), 1, dtype, [(0, *shape)])
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("shape", STRIDED[512] + PAIRS[512])
+@pytest.mark.parametrize("shape", STRIDED[512] + PAIRS[512] + SPLITS[512])
 def test_strided_512(dtype, shape):
     # pass 2 is the superstep along the outer axis (512, stride 8*64 elements)
     # and pass 1 the one along the middle axis (8)
@@ -95,6 +100,22 @@ def test_strided_512(dtype, shape):
 def test_strided_512_ragged(dtype, shape):
     # batch 3 of 512 x 2: 6 strided pencils of 512, stride 2, in one partial tile
     run_variant((3, 512, 2), 2, dtype, [(1, *shape)])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape", SPLITS[512])
+def test_split_pairs_512_inverse_in_place(dtype, shape):
+    # the inverse conjugates on load and scales on store (packed multiplies
+    # in the split form); both strided supersteps of a 3D transform (strides
+    # 32 and 512*32 elements), in place
+    run_variant((512, 512, 32), 3, dtype, [(1, *shape), (2, *shape)], direction=W.INVERSE, inplace=True)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape", CONTIG_SPLITS[512])
+def test_contig_split_512_inverse_in_place(dtype, shape):
+    # conjugate on load and scale on store in the split form, 2D 16 x 512
+    run_variant((3, 16, 512), 2, dtype, [(0, *shape)], direction=W.INVERSE, inplace=True)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
