@@ -195,6 +195,8 @@ cudaError_t launch_extra(int kind, int N, int E, int tile, const void *in, void 
 template <class S>
 cudaError_t launch_extra_variant(int kind, int N, int E, int tile, const void *in, void *out,
                                  const PassArgs &a, cudaStream_t st) {
+    if (kind == PASS_STRIDED && N == 512 && E == 32 && tile == 16)
+        return launch_strided<512, 32, 16, S, true>(in, out, a, st);
     if (kind == PASS_STRIDED && N == 1024 && E == 32 && tile == 8)
         return launch_strided<1024, 32, 8, S, true>(in, out, a, st);
     if (kind == PASS_STRIDED && N == 1024 && E == 32 && tile == 16)

@@ -391,8 +391,14 @@ int Plan::build_schedule() {
     if (r == 1 && d[0] > 4096) {
         const int64_t n = d[0];
         const int lg = ilog2(n);
-        const int64_t n1 = (int64_t)1 << ((lg + 1) / 2);  // contiguous length
-        const int64_t n2 = n / n1;                         // strided length
+        // complex64 at n = 2^20 splits 2048 (contiguous) x 512 (strided)
+        // rather than 1024 x 1024: the 512-point strided superstep with the
+        // inter-step twiddle runs at 1.61 ms per 512 x 2^20 execute against
+        // 2.11 ms for the 1024-point one, the 2048-point contiguous superstep
+        // costs 1.97 against 1.81 ms (3.57 vs 3.91 ms per execute)
+        const int lg1 = (lg == 20 && dtype == WSFFT_C32) ? 11 : (lg + 1) / 2;
+        const int64_t n1 = (int64_t)1 << lg1;  // contiguous length
+        const int64_t n2 = n / n1;             // strided length
         const float sc = axis_scale(n, dir, norm);
         // workspace holds `chunk` transforms (at most ~4 GiB: measured 5%
         // faster than 512 MiB chunks at 512 x 2^20, fewer launch tails;
@@ -404,7 +410,7 @@ int Plan::build_schedule() {
         a.kind = PASS_STRIDED;
         a.N = (int)n2;
         a.E = default_E((int)n2);
-        if (n2 == 1024 && dtype == WSFFT_C32) {
+        if ((n2 == 1024 || n2 == 512) && dtype == WSFFT_C32) {
             // measured fastest at n = 2^20: 32 values per thread, 16 pencils per block
             a.E = 32;
             a.tile = 16;

@@ -151,12 +151,18 @@ def test_1024_shapes(dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("settings", [[(0, 32, 8)], [(0, 32, 16)], [(1, 32, 8)], [(0, 32, 16), (1, 32, 8)]])
-def test_four_step_shapes(dtype, settings):
-    # 1D n = 2^20 = 1024 x 1024: pass 0 strided with the inter-step twiddle,
-    # pass 1 contiguous with the transposed store
-    run_variant((2, 1 << 20), 1, dtype, settings)
-    run_variant((1, 1 << 20), 1, dtype, settings, direction=W.INVERSE)
+@pytest.mark.parametrize("n,settings", [
+    (1 << 21, [(0, 32, 8)]),               # 2048 x 1024: 1024-point strided superstep, 8 pencils per block
+    (1 << 21, [(0, 32, 16)]),              # the same, 16 pencils per block
+    (1 << 19, [(1, 32, 8)]),               # 1024 x 512: 1024-point contiguous superstep, transposed store
+    (1 << 19, [(0, 32, 16), (1, 32, 8)]),  # and the 512-point strided one, 32 values per thread
+    (1 << 20, [(0, 32, 16)]),              # complex64 2048 x 512, 16-bit storage 1024 x 1024
+])
+def test_four_step_shapes(dtype, n, settings):
+    # 1D four-step split n = n1 (contiguous) x n2 (strided): pass 0 strided
+    # with the inter-step twiddle, pass 1 contiguous with the transposed store
+    run_variant((2, n), 1, dtype, settings)
+    run_variant((1, n), 1, dtype, settings, direction=W.INVERSE)
 
 
 
