@@ -87,6 +87,18 @@ typedef enum {
 } wsfft_norm;
 
 typedef enum {
+    /* spectral data in natural row-major order, the same layout as the
+     * spatial data (numpy's fftn) */
+    WSFFT_LAYOUT_NATURAL = 0,
+    /* spectral data with the last two axes swapped, the order in which the
+     * wafer holds the result after its two transposes (Section 4.2: each PE
+     * ends with a pencil of the second-to-last axis in memory): a rank-3
+     * n0 x n1 x n2 spectrum is stored as [n0][n2][n1], a rank-2 n0 x n1 one
+     * as [n1][n0] */
+    WSFFT_LAYOUT_SWAPPED = 1
+} wsfft_layout;
+
+typedef enum {
     WSFFT_SUCCESS = 0,
     WSFFT_ERR_INVALID_ARG = -1,   /* null/misaligned pointer, bad enum, bad rank */
     WSFFT_ERR_INVALID_SIZE = -2,  /* non-power-of-two or out-of-range axis */
@@ -113,6 +125,21 @@ int wsfft_plan_create(wsfft_plan *plan, const int64_t *dims, int rank, int dtype
 /* Change the normalisation (a wsfft_norm).  Section 4.2.
  * Errors: INVALID_ARG. */
 int wsfft_plan_set_norm(wsfft_plan plan, int norm);
+
+/* Choose the layout of the spectral side (a wsfft_layout): the forward
+ * writes its output in it, the inverse reads its input in it; the spatial
+ * side stays natural.  WSFFT_LAYOUT_SWAPPED needs rank 2 or 3 with both of
+ * the last two axes in [64, 4096]; it runs the first superstep with a
+ * transposing store into a plan-owned workspace (one array, at most 4 GiB of
+ * transforms at a time), so it moves the same bytes as the natural layout
+ * (three trips for rank 3, two for rank 2) and never uses the fused
+ * schedules of wsfft_plan_set_engine.  On this hardware the natural order
+ * costs nothing extra; the swapped one serves callers that work on the
+ * wafer's spectral layout.  Resets pass-shape choices
+ * (wsfft_plan_set_pass_variant).
+ * Errors: INVALID_ARG (bad enum), UNSUPPORTED (rank or sizes, ragged plan),
+ * ALLOC. */
+int wsfft_plan_set_layout(wsfft_plan plan, int layout);
 
 /* Enqueue the transform of `batch` arrays from `in` to `out` on `stream`.
  * in/out: device pointers to batch*prod(dims) elements of the plan's dtype.

@@ -61,6 +61,7 @@ struct Plan {
     // persistent engine state
     int sm_count = 0;
     int eng_grid = 0;
+    int layout = 0;                // wsfft_layout of the spectral side
     int engine_mode = 0;           // 0 one launch per superstep, 1 persistent, 2 pipelined, 3 warp-per-pencil
     int persist_grid = 0;          // persistent kernel blocks (all resident)
     void *d_items = nullptr;       // item tables of passes A and B

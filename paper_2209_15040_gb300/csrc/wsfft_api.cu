@@ -381,14 +381,127 @@ int Plan::build_schedule() {
     work_elems = 0;
     chunk = batch;
 
+    // kernel shapes of a one-launch contiguous or strided superstep
+    auto tune = [&](PassSpec &p, int64_t inner) {
+        if (p.kind == PASS_CONTIG && p.N == 512) {
+            // measured fastest at 512^3: 16 values per thread (radices
+            // 16, 16, 2), 8 pencils per block (32 values per thread
+            // matched it forward but lost 30% with the conjugate on load
+            // of the inverse); complex64 one pencil per warp (256-thread
+            // blocks, at the copy bandwidth), the 16-bit types as
+            // split-form pairs (one pair per warp, packed FP32x2
+            // butterflies: 13% faster there, the same in complex64)
+            p.E = 16;
+            p.tile = dtype == WSFFT_C32 ? 8 : SPLIT_TILE + 8;
+        }
+        if (p.N == 1024) {
+            // measured at 1024^3: 32 values per thread (radix 32 x 32, one
+            // exchange); contiguous: one warp per pencil, 8 per block;
+            // strided: 16 pencils per block at strides of 2^17 elements
+            // and more (128-byte rows), 8 below (16-bit storage there
+            // with 16 values per thread)
+            p.E = 32;
+            p.tile = 8;
+            if (p.kind == PASS_STRIDED) {
+                if (inner >= ((int64_t)1 << 17)) p.tile = 16;
+                else if (dtype != WSFFT_C32) p.E = 16;
+            }
+        }
+        if (p.kind == PASS_STRIDED && p.N == 512 && inner % 16 == 0) {
+            // measured fastest at 512^3: split-form pencil pairs (packed
+            // FP32x2 butterflies, two adjacent elements per access), 16
+            // values per pencil, 16 pencils per block, except for complex64
+            // at strides of 2^17 elements and more, where 32 values per
+            // thread for one pencil (one shared-memory exchange) match them
+            p.E = 16;
+            p.tile = SPLIT_TILE + 16;
+            if (dtype == WSFFT_C32 && inner >= ((int64_t)1 << 17)) {
+                p.E = 32;
+                p.tile = 16;
+            }
+        }
+    };
+
     // fused schedules: the two inner axes equal (n x n slabs); the pipelined
     // engine also runs the outer axis, so it needs a cube
-    if (r == 3 && engine_mode != 0 && d[1] == d[2] && engine_supports((int)d[1]) &&
+    if (layout == WSFFT_LAYOUT_NATURAL && r == 3 && engine_mode != 0 && d[1] == d[2] && engine_supports((int)d[1]) &&
         (engine_mode != 2 || d[0] == d[1]) && (engine_mode != 3 || wp_supports((int)d[1])) &&
         eng_grid > 0) {
         return build_engine(d[0], d[1], inv);
     }
-    if (r == 1 && d[0] > 4096) {
+    if (layout == WSFFT_LAYOUT_SWAPPED) {
+        // Spectral side with the last two axes swapped (the wafer's order,
+        // Section 4.2).  The superstep along the last axis of the natural
+        // side stores its pencils transposed (the four-step's staged store:
+        // pencil (plane, row) element k to plane*N*rows + k*rows + row) into
+        // the workspace, which turns the natural [a][b][c] into [a][c][b] or
+        // back; the next axis is then contiguous on both sides of the swap,
+        // and the first axis of a rank-3 array keeps its stride.
+        //   forward:  c with the transposed store (in -> work), b contiguous
+        //             (work -> out), a strided (out, in place)
+        //   inverse:  b with the transposed store (in -> work), c contiguous
+        //             (work -> out), a strided (out, in place)
+        const int64_t A = rank == 3 ? dims[0] : 1, B = dims[rank - 2], C = dims[rank - 1];
+        const int64_t total = A * B * C;
+        const int64_t per = total * elem_bytes(dtype);
+        chunk = std::max<int64_t>(1, std::min<int64_t>(batch, ((int64_t)4096 << 20) / per));
+        work_elems = chunk * total;
+        const int64_t n_t = inv ? B : C;  // axis of the transposing superstep
+        const int64_t n_c = inv ? C : B;  // the other of the last two axes
+        PassSpec t{};
+        t.kind = PASS_CONTIG;
+        t.N = (int)n_t;
+        t.E = default_E(t.N);
+        if (t.N == 1024 && dtype == WSFFT_C32) {
+            t.E = 32;  // as in the four-step: one warp per pencil, 8 per block
+            t.tile = 8;
+        }
+        t.variant = true;
+        t.inner = 1;
+        t.npencils_per_batch = A * n_c;
+        t.trans_rows = n_c;
+        t.src = SRC_IN;
+        t.dst = DST_WORK;
+        t.conj_in = inv;
+        t.scale = axis_scale(n_t, dir, norm);
+        t.transform_elems = total;
+        PassSpec c{};
+        c.kind = PASS_CONTIG;
+        c.N = (int)n_c;
+        c.E = default_E(c.N);
+        tune(c, 1);
+        c.inner = 1;
+        c.npencils_per_batch = A * n_t;
+        c.src = SRC_WORK;
+        c.dst = DST_OUT;
+        c.scale = axis_scale(n_c, dir, norm);
+        c.transform_elems = total;
+        passes.push_back(t);
+        passes.push_back(c);
+        if (A > 1) {
+            PassSpec a{};
+            a.kind = PASS_STRIDED;
+            a.N = (int)A;
+            a.E = default_E(a.N);
+            tune(a, B * C);
+            a.inner = B * C;
+            a.npencils_per_batch = B * C;
+            a.src = SRC_OUT;
+            a.dst = DST_OUT;
+            a.scale = axis_scale(A, dir, norm);
+            a.transform_elems = total;
+            passes.push_back(a);
+        }
+        passes.back().conj_out = inv;
+        if (dtype == WSFFT_C32 && norm != WSFFT_NORM_ORTHO) {
+            double total_scale = 1.0;
+            for (auto &q : passes) {
+                total_scale *= q.scale;
+                q.scale = 1.f;
+            }
+            passes.back().scale = (float)total_scale;
+        }
+    } else if (r == 1 && d[0] > 4096) {
         const int64_t n = d[0];
         const int lg = ilog2(n);
         // complex64 at n = 2^20 splits 2048 (contiguous) x 512 (strided)
@@ -458,43 +571,7 @@ int Plan::build_schedule() {
             p.N = (int)d[ax];
             p.E = default_E(p.N);
             p.variant = false;
-            if (p.kind == PASS_CONTIG && p.N == 512) {
-                // measured fastest at 512^3: 16 values per thread (radices
-                // 16, 16, 2), 8 pencils per block (32 values per thread
-                // matched it forward but lost 30% with the conjugate on load
-                // of the inverse); complex64 one pencil per warp (256-thread
-                // blocks, at the copy bandwidth), the 16-bit types as
-                // split-form pairs (one pair per warp, packed FP32x2
-                // butterflies: 13% faster there, the same in complex64)
-                p.E = 16;
-                p.tile = dtype == WSFFT_C32 ? 8 : SPLIT_TILE + 8;
-            }
-            if (p.N == 1024) {
-                // measured at 1024^3: 32 values per thread (radix 32 x 32, one
-                // exchange); contiguous: one warp per pencil, 8 per block;
-                // strided: 16 pencils per block at strides of 2^17 elements
-                // and more (128-byte rows), 8 below (16-bit storage there
-                // with 16 values per thread)
-                p.E = 32;
-                p.tile = 8;
-                if (p.kind == PASS_STRIDED) {
-                    if (inner >= ((int64_t)1 << 17)) p.tile = 16;
-                    else if (dtype != WSFFT_C32) p.E = 16;
-                }
-            }
-            if (p.kind == PASS_STRIDED && p.N == 512 && inner % 16 == 0) {
-                // measured fastest at 512^3: split-form pencil pairs (packed
-                // FP32x2 butterflies, two adjacent elements per access), 16
-                // values per pencil, 16 pencils per block, except for complex64
-                // at strides of 2^17 elements and more, where 32 values per
-                // thread for one pencil (one shared-memory exchange) match them
-                p.E = 16;
-                p.tile = SPLIT_TILE + 16;
-                if (dtype == WSFFT_C32 && inner >= ((int64_t)1 << 17)) {
-                    p.E = 32;
-                    p.tile = 16;
-                }
-            }
+            tune(p, inner);
             p.inner = inner;
             p.npencils_per_batch = total / d[ax];
             p.src = ax == r - 1 ? SRC_IN : SRC_OUT;
@@ -840,6 +917,31 @@ int wsfft_plan_set_norm(wsfft_plan plan, int norm) {
     if (p->ragged) return WSFFT_ERR_UNSUPPORTED;
     p->norm = norm;
     return p->build_schedule();
+}
+
+int wsfft_plan_set_layout(wsfft_plan plan, int layout) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || (layout != WSFFT_LAYOUT_NATURAL && layout != WSFFT_LAYOUT_SWAPPED)) return WSFFT_ERR_INVALID_ARG;
+    if (p->ragged) return WSFFT_ERR_UNSUPPORTED;
+    if (layout == WSFFT_LAYOUT_SWAPPED) {
+        // the transposing store is built for pencils of 64..4096 points, and
+        // its tiles need the row count to be a multiple of their pencils per
+        // block (at most 32, so rows >= 64 suffice)
+        if (p->rank < 2) return WSFFT_ERR_UNSUPPORTED;
+        for (int i = p->rank - 2; i < p->rank; ++i)
+            if (p->dims[i] < 64 || p->dims[i] > 4096) return WSFFT_ERR_UNSUPPORTED;
+    }
+    const int old_layout = p->layout;
+    const auto old_over = p->overrides;
+    p->layout = layout;
+    p->overrides.clear();
+    const int rc = p->build_schedule();
+    if (rc != WSFFT_SUCCESS) {
+        p->layout = old_layout;
+        p->overrides = old_over;
+        p->build_schedule();
+    }
+    return rc;
 }
 
 int wsfft_execute(wsfft_plan plan, const void *in, void *out, wsfft_stream stream) {

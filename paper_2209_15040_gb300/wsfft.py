@@ -20,6 +20,7 @@ import torch
 C32, C16F, C16BF = 0, 1, 2
 FORWARD, INVERSE = -1, 1
 NORM_PAPER, NORM_NONE, NORM_ORTHO, NORM_FORWARD = 0, 1, 2, 3
+LAYOUT_NATURAL, LAYOUT_SWAPPED = 0, 1
 NORMS = {"paper": NORM_PAPER, "none": NORM_NONE, "ortho": NORM_ORTHO, "forward": NORM_FORWARD}
 
 SUCCESS = 0
@@ -36,7 +37,7 @@ _lib = None
 _lock = threading.Lock()
 
 EXPORTS = (
-    "wsfft_plan_create", "wsfft_plan_set_norm", "wsfft_execute", "wsfft_execute_host",
+    "wsfft_plan_create", "wsfft_plan_set_norm", "wsfft_plan_set_layout", "wsfft_execute", "wsfft_execute_host",
     "wsfft_destroy", "wsfft_plan_create_ragged", "wsfft_execute_ragged", "wsfft_autotune",
     "wsfft_plan_sync_status", "wsfft_plan_passes", "wsfft_plan_profile",
     "wsfft_plan_set_pass_variant", "wsfft_plan_set_engine", "wsfft_plan_set_wait_test",
@@ -65,6 +66,7 @@ def lib():
         P, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         L.wsfft_plan_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(i64), ci, ci, ci, i64]
         L.wsfft_plan_set_norm.argtypes = [P, ci]
+        L.wsfft_plan_set_layout.argtypes = [P, ci]
         L.wsfft_execute.argtypes = [P, P, P, P]
         L.wsfft_execute_host.argtypes = [P, P, P, P]
         L.wsfft_destroy.argtypes = [P]
@@ -150,6 +152,10 @@ class Plan:
         _check(lib().wsfft_plan_passes(self._h, ctypes.byref(n), ctypes.byref(b)),
                "wsfft_plan_passes")
         return n.value, b.value
+
+    def set_layout(self, layout: int) -> None:
+        """Spectral-side layout: LAYOUT_NATURAL or LAYOUT_SWAPPED (last two axes swapped)."""
+        _check(lib().wsfft_plan_set_layout(self._h, int(layout)), "wsfft_plan_set_layout")
 
     def set_pass_variant(self, pass_index: int, values_per_thread: int, tile: int) -> None:
         """Kernel shape of one pass (0, 0 = default); see wsfft_plan_set_pass_variant."""

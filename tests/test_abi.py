@@ -71,6 +71,7 @@ def test_host_validation_without_gpu(lib):
     assert lib.wsfft_plan_create(None, None, 3, 0, -1, 1) == W.ERR_INVALID_ARG
     assert lib.wsfft_execute(None, None, None, None) == W.ERR_INVALID_ARG
     assert lib.wsfft_plan_set_norm(None, 0) == W.ERR_INVALID_ARG
+    assert lib.wsfft_plan_set_layout(None, W.LAYOUT_SWAPPED) == W.ERR_INVALID_ARG
     assert lib.wsfft_plan_sync_status(None, None) == W.ERR_INVALID_ARG
     assert lib.wsfft_destroy(None) == W.SUCCESS
 
