@@ -590,9 +590,24 @@ def main():
         torch.cuda.synchronize()
         barrier(world)
         dt = allmax(world, time.perf_counter() - t0)
+        # the host link as it ran during this leg (one 1 GiB copy each way,
+        # the same pinned buffers): the floor the end-to-end number sits on
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        with torch.cuda.stream(stream):
+            x.copy_(hx, non_blocking=True)
+            ev[1].record(stream)
+            hy.copy_(x, non_blocking=True)
+            ev[2].record(stream)
+        torch.cuda.synchronize()
+        nbytes = ELEMS * 8
+        h2d = nbytes / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e9
+        d2h = nbytes / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9
         e2e = {"value": round(dt / esteps * 1e6 / 2 / world, 2), "unit": "us",
                "h2d_bytes_per_step": 2 * ELEMS * 8, "d2h_bytes_per_step": 2 * ELEMS * 8,
-               "steps": esteps, "entry": "wsfft_execute_host (pinned host buffers)"}
+               "steps": esteps, "entry": "wsfft_execute_host (pinned host buffers)",
+               "link_h2d_gbs": round(h2d, 1), "link_d2h_gbs": round(d2h, 1),
+               "copy_floor_us": round((nbytes / h2d + nbytes / d2h) / 1e3, 1)}
 
     sizes = None
     if not args.no_sizes and world == 1:
