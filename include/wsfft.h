@@ -190,7 +190,8 @@ int wsfft_execute_ragged(wsfft_plan plan, const void *const *in, void *const *ou
 /* Time the kernel variants that apply to this plan on `stream` (with
  * temporary buffers) and keep the fastest; results are cached in the JSON
  * file named by WSFFT_TUNE_CACHE (if set), keyed by device name, SM count,
- * shape, dtype and direction.  Errors: ALLOC, CUDA. */
+ * shape, batch, dtype, direction, normalisation and spectral layout.
+ * Errors: ALLOC, CUDA. */
 int wsfft_autotune(wsfft_plan plan, wsfft_stream stream);
 
 /* Choose the kernel shape of pass `pass` (0-based, in launch order) of this

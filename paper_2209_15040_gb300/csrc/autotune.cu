@@ -39,9 +39,9 @@ std::string plan_key(const Plan &p) {
     std::string name = "unknown";
     if (cudaGetDeviceProperties(&prop, p.device) == cudaSuccess) name = prop.name;
     char buf[512];
-    snprintf(buf, sizeof buf, "%s|sm%d|%lldx%lldx%lld|r%d|b%lld|t%d|d%d|n%d", name.c_str(), p.sm_count,
+    snprintf(buf, sizeof buf, "%s|sm%d|%lldx%lldx%lld|r%d|b%lld|t%d|d%d|n%d|l%d", name.c_str(), p.sm_count,
              (long long)p.dims[0], (long long)p.dims[1], (long long)p.dims[2], p.rank, (long long)p.batch,
-             p.dtype, p.dir, p.norm);
+             p.dtype, p.dir, p.norm, p.layout);
     return buf;
 }
 

@@ -796,6 +796,10 @@ int Plan::run_host_pipelined(const void *hin, void *hout, cudaStream_t st) {
         PassSpec px = passes[2], py = passes[1];
         py.conj_out = px.conj_out;
         px.conj_out = false;
+        // launch order here is z, x, y: the rule on programmatic dependent
+        // launch after a split-form contiguous launch follows that order
+        px.no_pdl = passes[0].kind == PASS_CONTIG && passes[0].tile >= SPLIT_TILE;
+        py.no_pdl = false;
         int rc = run_pass(px, db, I);
         if (rc != WSFFT_SUCCESS) return rc;
         // out: the y superstep of each slab chunk, then its copy back

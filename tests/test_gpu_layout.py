@@ -144,3 +144,31 @@ def test_swapped_layout_host_buffers():
     y = hy.numpy().astype(np.complex128).reshape(_swapped_shape(shape))
     ref = np.swapaxes(oracle.fftn(xc, rank=3), -1, -2)
     assert oracle.rel_l2(y, ref) < TOL["c32"]
+
+
+def test_swapped_layout_autotune_cache(tmp_path, monkeypatch):
+    # the tuning cache keeps swapped and natural plans of one shape apart
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("WSFFT_TUNE_CACHE", str(cache))
+    shape = (2, 256, 512)
+    xs, xc = seeded(shape, 14, "normal", "c32")
+    x = to_device(xs, "c32")
+    y = torch.empty_like(x)
+    plan = W.Plan(shape[1:], W.C32, W.FORWARD, 2)
+    plan.set_layout(W.LAYOUT_SWAPPED)
+    plan.autotune()
+    assert len(cache.read_text().strip().splitlines()) == 1
+    plan.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    plan.close()
+    ref = oracle.fftn(xc, rank=2)
+    got = to_host_c128(y, "c32").reshape(_swapped_shape(shape))
+    assert oracle.rel_l2(got, np.swapaxes(ref, -1, -2)) < TOL["c32"]
+    plan2 = W.Plan(shape[1:], W.C32, W.FORWARD, 2)
+    plan2.autotune()
+    assert len(cache.read_text().strip().splitlines()) == 2
+    y.zero_()
+    plan2.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    plan2.close()
+    assert oracle.rel_l2(to_host_c128(y, "c32"), ref) < TOL["c32"]
