@@ -1,0 +1,61 @@
+"""Host logic of bench.py that needs no GPU: the source fingerprint that
+decides whether recorded DRAM counters still describe the kernels, the
+lookup of those counters, and the peak-bandwidth fallback."""
+import json
+import os
+
+import bench
+
+
+def _tree(tmp_path, files):
+    d = tmp_path / "paper_2209_15040_gb300" / "csrc"
+    d.mkdir(parents=True, exist_ok=True)
+    for name, text in files.items():
+        (d / name).write_text(text)
+    return tmp_path
+
+
+def test_fingerprint_follows_kernel_sources(tmp_path, monkeypatch):
+    root = _tree(tmp_path, {"a.cu": "x", "b.cuh": "y", "c.h": "z", "notes.txt": "ignored"})
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    h0 = bench.source_sha256()
+    (root / "paper_2209_15040_gb300" / "csrc" / "notes.txt").write_text("changed")
+    assert bench.source_sha256() == h0  # only .cu/.cuh/.h count
+    (root / "paper_2209_15040_gb300" / "csrc" / "b.cuh").write_text("y2")
+    assert bench.source_sha256() != h0
+    (root / "paper_2209_15040_gb300" / "csrc" / "b.cuh").write_text("y")
+    assert bench.source_sha256() == h0
+    (root / "paper_2209_15040_gb300" / "csrc" / "b2.cuh").write_text("")
+    assert bench.source_sha256() != h0  # a new file counts too
+
+
+def test_traffic_lookup_only_for_matching_sources(tmp_path, monkeypatch):
+    root = _tree(tmp_path, {"k.cu": "kernel"})
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.kernel_traffic(0) is None  # no record
+    (root / "profiles").mkdir()
+    rec = {"source_sha256": bench.source_sha256(), "c32_512_pass0": 1.5e9, "c32_512_pass2": 2.0e9}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.kernel_traffic(0) == 1.5e9
+    assert bench.kernel_traffic(2) == 2.0e9
+    assert bench.kernel_traffic(1) is None  # not recorded
+    (root / "paper_2209_15040_gb300" / "csrc" / "k.cu").write_text("kernel, edited")
+    assert bench.kernel_traffic(0) is None  # counters of older kernels are not reported
+
+
+def test_recorded_traffic_is_a_plausible_launch():
+    # the committed record, when it matches the sources, holds about one read
+    # and one write of the 1 GiB array per launch (not a multiple of it)
+    path = os.path.join(bench.ROOT, "profiles", "traffic.json")
+    with open(path) as f:
+        rec = json.load(f)
+    for i in range(3):
+        v = rec.get("c32_512_pass%d" % i)
+        assert v is None or 0.9 * 2 ** 31 < v < 1.2 * 2 ** 31, (i, v)
+
+
+def test_peak_fallback_without_measured_file(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6791.0}))
+    assert bench.peaks() == (6791.0, "measured")
