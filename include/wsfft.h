@@ -90,11 +90,11 @@ typedef enum {
     /* spectral data in natural row-major order, the same layout as the
      * spatial data (numpy's fftn) */
     WSFFT_LAYOUT_NATURAL = 0,
-    /* spectral data with the last two axes swapped, the order in which the
-     * wafer holds the result after its two transposes (Section 4.2: each PE
-     * ends with a pencil of the second-to-last axis in memory): a rank-3
-     * n0 x n1 x n2 spectrum is stored as [n0][n2][n1], a rank-2 n0 x n1 one
-     * as [n1][n0] */
+    /* spectral data with the last two axes swapped: a rank-3 n0 x n1 x n2
+     * spectrum is stored as [n0][n2][n1], a rank-2 n0 x n1 one as [n1][n0].
+     * The middle axis ends contiguous, as on the wafer after its two
+     * transposes (Section 4.2: each PE ends holding a pencil of that axis);
+     * the two axes the wafer spreads over its mesh keep the input's order */
     WSFFT_LAYOUT_SWAPPED = 1
 } wsfft_layout;
 
@@ -134,8 +134,8 @@ int wsfft_plan_set_norm(wsfft_plan plan, int norm);
  * transforms at a time), so it moves the same bytes as the natural layout
  * (three trips for rank 3, two for rank 2) and never uses the fused
  * schedules of wsfft_plan_set_engine.  On this hardware the natural order
- * costs nothing extra; the swapped one serves callers that work on the
- * wafer's spectral layout.  Resets pass-shape choices
+ * costs nothing extra; the swapped one serves callers that work on a
+ * spectrum with the middle axis in memory.  Resets pass-shape choices
  * (wsfft_plan_set_pass_variant).
  * Errors: INVALID_ARG (bad enum), UNSUPPORTED (rank or sizes, ragged plan),
  * ALLOC. */

@@ -1,7 +1,7 @@
-"""GPU parity of the swapped spectral layout (the wafer's order after its
-two transposes, Section 4.2): the forward writes its result with the last
-two axes swapped, the inverse reads its input that way; the spatial side is
-natural.  Compared with the FP64 oracle's natural result with those two
+"""GPU parity of the swapped spectral layout (the middle axis in memory, as
+on the wafer after its two transposes, Section 4.2): the forward writes its
+result with the last two axes swapped, the inverse reads its input that way;
+the spatial side is natural.  Compared with the FP64 oracle's natural result with those two
 axes swapped, for every storage type, rank 2 and 3, batches, in place and
 out of place, and sizes that reach the tuned 512-point kernel shapes."""
 import numpy as np
