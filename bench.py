@@ -68,6 +68,15 @@ def kernel_traffic(pass_index: int):
     return rec.get("c32_512_pass%d" % pass_index)
 
 
+def device_info(dev):
+    """GPU name and SM count of the device the bench ran on (None if unknown)."""
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return {"name": p.name, "sms": p.multi_processor_count}
+    except Exception:
+        return None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -532,6 +541,10 @@ def main():
     inv.execute(y.data_ptr(), y.data_ptr(), stream)
     torch.cuda.synchronize()
     rt32 = float(torch.linalg.vector_norm(y - x) / torch.linalg.vector_norm(x))
+    try:
+        rt32_max_abs = float((y - x).abs().max())
+    except Exception:  # reporting only: never fail the bench over it
+        rt32_max_abs = None
 
     # dominant kernel: pass index with the largest mean time
     pass_ms = [[] for _ in range(npass)]
@@ -651,6 +664,8 @@ def main():
                          "per_pass_ms": [round(v, 4) for v in mean_ms],
                          "bytes_per_launch": bytes_launch, "peak_kind": peak_kind},
             "rel_l2_roundtrip_c32": rt32,
+            "max_abs_roundtrip_c32": rt32_max_abs,
+            "device": device_info(dev),
             "half_storage": half,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,

@@ -59,3 +59,9 @@ def test_peak_fallback_without_measured_file(tmp_path, monkeypatch):
     assert bench.peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6791.0}))
     assert bench.peaks() == (6791.0, "measured")
+
+
+def test_device_info_is_safe_without_a_gpu():
+    import torch
+    info = bench.device_info(torch.device("cuda", 0))
+    assert info is None or (isinstance(info["name"], str) and info["sms"] > 0)
