@@ -164,8 +164,11 @@ int wsfft_execute(wsfft_plan plan, const void *in, void *out, wsfft_stream strea
 int wsfft_execute_host(wsfft_plan plan, const void *host_in, void *host_out,
                        wsfft_stream stream);
 
-/* Release the plan and every device allocation it owns.  Synchronises the
- * plan's device first.  NULL is accepted.  Errors: CUDA. */
+/* Release the plan and every device allocation it owns.  Waits first for
+ * the plan's own work: every stream the plan was executed on, up to its last
+ * execute there (executes enqueued while a stream was being captured into a
+ * graph are the caller's to wait for), and the plan's internal streams; other
+ * work on the device is not waited for.  NULL is accepted.  Errors: CUDA. */
 int wsfft_destroy(wsfft_plan plan);
 
 /* Plan for `count` independent rank-3 transforms of uneven shapes
@@ -212,6 +215,13 @@ int wsfft_plan_set_pass_variant(wsfft_plan plan, int pass, int values_per_thread
 /* Choose the schedule of a rank-3 transform n0 x n x n (n in {128, 256, 512,
  * 1024}, any n0; the pipelined engine needs n0 == n):
  *   0 (default): one launch per superstep (three trips through HBM);
+ *   4 (n in {256, 512}): two trips through HBM -- one thread-block cluster
+ *      per n x n slab runs its z superstep, meets at a cluster barrier, and
+ *      runs its y superstep on the slab as the z tiles left it in L2; then
+ *      one launch runs the outer axis (Sections 4.2-4.3 with the
+ *      redistribution between z and y kept inside a cluster).  At 512^3 it
+ *      measured slower than mode 0 on GB300 (fused pass 0.70 ms against
+ *      0.64 ms for the two launches it replaces), so it is an option;
  *   3 (n <= 512): two trips through HBM with warp-per-pencil
  *      kernels -- a persistent kernel runs the supersteps along the two inner
  *      axes slab by slab, re-reading each slab from L2, then one launch runs
@@ -268,14 +278,26 @@ int wsfft_plan_launch_times(wsfft_plan plan, float *ms, int capacity, int *count
  *   n: 128, 256 or 512; batch * n <= 4096.  Larger sizes return
  *   WSFFT_ERR_INVALID_SIZE; null or misaligned pointers and bad directions
  *   return WSFFT_ERR_INVALID_ARG.
- * The first call on each device does that device's set-up (table upload,
- * symbol lookup, occupancy query) with the device current; make it before
- * any stream capture.  All calls on a device share the scratch array, which
- * keeps the last call's contents (each call clears the counters it uses):
- * calls that overlap on the GPU race and must not be made.
+ * The first call on each device does that device's set-up (table upload on
+ * `stream`, which it then synchronises, symbol lookup, occupancy query) with
+ * the device current; make it before any stream capture.  All calls on a
+ * device share the scratch array, which keeps the last call's contents (each
+ * call clears the counters it uses): calls that overlap on the GPU race and
+ * must not be made.  A bounded device-side wait that runs out leaves that
+ * call's output incomplete and is reported only by
+ * wsfft_noalloc_sync_status.
  * Errors: INVALID_ARG, INVALID_SIZE, UNSUPPORTED, CUDA. */
 int wsfft_execute_cube_noalloc(const void *in, void *out, int64_t n, int64_t batch,
                                int direction, wsfft_stream stream);
+
+/* Report and clear the status word of wsfft_execute_cube_noalloc on the
+ * current device: synchronises `stream`, then returns WSFFT_ERR_DEVICE_TIMEOUT
+ * if a bounded device-side wait of any call since the last report ran out
+ * (that call's output is incomplete), else WSFFT_SUCCESS (also when no call
+ * has run on this device).  Allocates nothing.  Like the entry point it
+ * reports on, it has no counterpart in the paper.  Errors: CUDA, UNSUPPORTED
+ * (device index beyond the library's table of devices). */
+int wsfft_noalloc_sync_status(wsfft_stream stream);
 
 /* Static text for a status code. */
 const char *wsfft_status_string(int status);

@@ -2,8 +2,9 @@
 // timing them, and remember the choice.
 //
 // Search (greedy, a few dozen executes): every cube schedule the shape
-// supports (one launch per superstep, and the two-trip persistent,
-// pipelined and warp-per-pencil schedules), then, for the fastest, each
+// supports (the cluster-fused two-trip schedule, one launch per superstep,
+// and the two-trip persistent, pipelined and warp-per-pencil schedules),
+// then, for the fastest, each
 // one-launch pass in turn over the (values per thread, pencils per block)
 // shapes the library instantiates for its axis length.  Every candidate runs
 // on temporary buffers of the plan's size: two warm-up executes, then the
@@ -180,7 +181,7 @@ extern "C" int wsfft_autotune(wsfft_plan plan, wsfft_stream stream) {
     const auto saved_over = p->overrides;
     Choice best;
     double best_us = 1e300;
-    for (int mode : {0, 1, 2, 3}) {
+    for (int mode : {4, 0, 1, 2, 3}) {
         Choice c;
         c.mode = mode;
         if (apply(*p, c) != WSFFT_SUCCESS) continue;

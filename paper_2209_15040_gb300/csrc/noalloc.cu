@@ -22,10 +22,17 @@
 // two streams, or from two host threads -- race on the counters and must not
 // be issued.
 //
-// Set-up: the first call on each device (with that device current) uploads
-// the twiddle tables with cudaMemcpyToSymbol, looks up the arrays' device
-// addresses with cudaGetSymbolAddress and queries the occupancy of the
-// persistent kernel.  Make that first call before any stream capture.
+// Set-up: the first call on each device (with that device current) copies
+// the twiddle tables into their array on the caller's stream and waits for
+// that stream, looks up the arrays' device addresses with
+// cudaGetSymbolAddress and queries the occupancy of the persistent kernel.
+// Make that first call before any stream capture.
+//
+// Timeouts: pass A's waits are bounded (one second each); a wait that runs
+// out sets a status word in a third static array and its tile is skipped, so
+// that call's result is incomplete.  The call itself cannot see this (it
+// does not wait for the GPU); wsfft_noalloc_sync_status reports and clears
+// it.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -34,6 +41,7 @@
 
 #include "../../include/wsfft.h"
 #include "fft_core.cuh"
+#include "host_roots.h"
 #include "pass_desc.h"
 #include "persist.cuh"
 
@@ -46,6 +54,10 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) uint32_t g_noalloc_ctr[1 + kMaxSlabs];
 static __device__ __align__(256) float2 g_noalloc_tw[kTwElems];
+// Status word of the bounded waits: set to 1 when a wait of pass A runs out
+// (the tiles that wait skip their work, so the result of that call is
+// incomplete).  Sticky until wsfft_noalloc_sync_status reads and clears it.
+static __device__ __align__(256) int g_noalloc_status;
 
 // schedules used: persistent pass A per n, and the x superstep per n
 struct CubeShape {
@@ -59,48 +71,15 @@ constexpr CubeShape kShapes[3] = {{128, 16, 64, 16, 0}, {256, 16, 32, 16, 0}, {5
 
 struct DevState {
     bool ready = false;
-    int status = 0;
     uint32_t *ctr = nullptr;
     float2 *tw = nullptr;
+    int *status = nullptr;
     int tw_off[3][2] = {};   // [shape][pass A / pass B] offset in the twiddle array
     int grid[3] = {};
 };
 
 DevState g_dev[kMaxDevices];
 std::mutex g_mu;
-
-// exp(-2*pi*i*m/n), evaluated in long double on the angle folded into
-// [0, pi/2] by quadrant, then rounded to float.
-float2 root_ld(int64_t m, int64_t n) {
-    m %= n;
-    if (m < 0) m += n;
-    const int64_t q = (4 * m) / n;
-    const long double f = (long double)(4 * m - q * n) / (long double)n;  // [0, 1)
-    const long double a = 1.57079632679489661923132169163975144L * f;
-    const long double c = cosl(a), s = sinl(a);
-    long double cr, sr;
-    switch (q) {
-        case 0: cr = c; sr = s; break;
-        case 1: cr = -s; sr = c; break;
-        case 2: cr = -c; sr = -s; break;
-        default: cr = s; sr = -c; break;
-    }
-    return make_float2((float)cr, (float)-sr);
-}
-
-int fill_stage_table(float2 *dst, int cap, int N, int E) {
-    const int size = sched_tw_size(N, E);
-    if (size + 1 > cap) return -1;
-    const int ns = sched_nstages(N, E);
-    for (int s = 1; s < ns; ++s) {
-        const int R = sched_radix(N, E, s), Ns = sched_ns_before(N, E, s);
-        const int off = sched_tw_offset(N, E, s);
-        for (int r = 1; r < R; ++r)
-            for (int k = 0; k < Ns; ++k) dst[off + (r - 1) * Ns + k] = root_ld((int64_t)r * k, (int64_t)Ns * R);
-    }
-    dst[size] = make_float2(0.f, 0.f);
-    return size + 1;
-}
 
 // Tile order of pass A (the same rule as the plan builder's): slab j's
 // contiguous tiles, then the strided tiles of slab j - lag.  Decoded from
@@ -206,9 +185,10 @@ cudaError_t launch_a(const EngArgs &a, int per, int U, int lag, int grid, cudaSt
     return cudaGetLastError();
 }
 
-// Once per device, with that device current: tables, symbol addresses,
-// occupancy.  Returns a wsfft_status.
-int setup_device(int dev, DevState &d) {
+// Once per device, with that device current: tables (copied on `st`, which
+// is then synchronised), symbol addresses, occupancy.  Returns a
+// wsfft_status.
+int setup_device(int dev, DevState &d, cudaStream_t st) {
     static float2 host_tw[kTwElems];  // static: set-up allocates nothing either
     int off = 0;
     for (int s = 0; s < 3; ++s) {
@@ -224,13 +204,21 @@ int setup_device(int dev, DevState &d) {
             off += (used + 1) & ~1;  // keep 16-byte alignment
         }
     }
-    if (cudaMemcpyToSymbol(g_noalloc_tw, host_tw, sizeof(float2) * off) != cudaSuccess) return WSFFT_ERR_CUDA;
+    if (cudaMemcpyToSymbolAsync(g_noalloc_tw, host_tw, sizeof(float2) * off, 0, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return WSFFT_ERR_CUDA;
+    // host code sees only host-side stand-ins for the arrays: their device
+    // addresses come from the runtime, per device
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_ctr) != cudaSuccess || !p) return WSFFT_ERR_CUDA;
     d.ctr = static_cast<uint32_t *>(p);
     p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_tw) != cudaSuccess || !p) return WSFFT_ERR_CUDA;
     d.tw = static_cast<float2 *>(p);
+    p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_status) != cudaSuccess || !p) return WSFFT_ERR_CUDA;
+    d.status = static_cast<int *>(p);
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return WSFFT_ERR_CUDA;
     if (setup_kernel<128, 16, 64>(sms, &d.grid[0]) != cudaSuccess) return WSFFT_ERR_CUDA;
@@ -239,10 +227,6 @@ int setup_device(int dev, DevState &d) {
     d.ready = true;
     return WSFFT_SUCCESS;
 }
-
-// Status word the kernel's bounded waits write to if one ever runs out (the
-// waits only depend on tiles of the same call, so this needs a faulty GPU).
-static __device__ __align__(256) int g_noalloc_status;
 
 }  // namespace
 }  // namespace wsfft
@@ -265,15 +249,9 @@ extern "C" int wsfft_execute_cube_noalloc(const void *in, void *out, int64_t n, 
     {
         std::lock_guard<std::mutex> lk(g_mu);
         if (!d.ready) {
-            const int rc = setup_device(dev, d);
+            const int rc = setup_device(dev, d, (cudaStream_t)stream);
             if (rc != WSFFT_SUCCESS) return rc;
         }
-    }
-    int *status = nullptr;
-    {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_status) != cudaSuccess || !p) return WSFFT_ERR_CUDA;
-        status = static_cast<int *>(p);
     }
     cudaStream_t st = (cudaStream_t)stream;
     const CubeShape &cs = kShapes[s];
@@ -291,7 +269,7 @@ extern "C" int wsfft_execute_cube_noalloc(const void *in, void *out, int64_t n, 
     a.items = nullptr;
     a.nitems = 2 * per * U;
     a.ctr = d.ctr;
-    a.status = status;
+    a.status = d.status;
     a.c_src = in;
     a.c_dst = out;
     a.s_src = out;
@@ -327,4 +305,24 @@ extern "C" int wsfft_execute_cube_noalloc(const void *in, void *out, int64_t n, 
     b.sy = inv ? -sc : sc;
     e = launch_pass_c32(PASS_STRIDED, (int)n, cs.eb, cs.tileb, false, out, out, b, st);
     return e == cudaSuccess ? WSFFT_SUCCESS : WSFFT_ERR_CUDA;
+}
+
+extern "C" int wsfft_noalloc_sync_status(wsfft_stream stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WSFFT_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return WSFFT_ERR_UNSUPPORTED;
+    int *status = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_dev[dev].ready) return WSFFT_SUCCESS;  // no call has run on this device
+        status = g_dev[dev].status;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return WSFFT_ERR_CUDA;
+    if (h != 0 && (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess))
+        return WSFFT_ERR_CUDA;
+    return h == 0 ? WSFFT_SUCCESS : WSFFT_ERR_DEVICE_TIMEOUT;
 }

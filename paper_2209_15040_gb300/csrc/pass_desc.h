@@ -70,6 +70,7 @@ enum PassKind {
     PASS_PERSIST_A = 4,  // persistent kernel: z and y of every slab
     PASS_WP_A = 5,       // warp-per-pencil persistent kernel: z and y of every slab
     PASS_WP_B = 6,       // warp-per-pencil strided superstep: x
+    PASS_SLAB_A = 7,     // cluster-fused z and y of every n x n slab (slab_cluster.cuh)
 };
 
 // Launch one superstep.  variant: contiguous -> transposed store,

@@ -416,7 +416,7 @@ struct SplitPair<__nv_bfloat162> {
     }
 };
 
-template <class S, int W, bool PLAIN>
+template <class S, int W, bool PLAIN, int LOP = OP_DEF, int SOP = OP_DEF>
 struct StridedSplitAcc {
     using value_type = cpair;
     using PT = typename SplitPair<S>::T;
@@ -428,7 +428,7 @@ struct StridedSplitAcc {
     float ci, sx, sy;
     bool active;
     __device__ __forceinline__ cpair gload(int k) const {
-        cpair v = active ? SplitPair<S>::load(in + (int64_t)k * stride)
+        cpair v = active ? SplitPair<S>::template load<LOP>(in + (int64_t)k * stride)
                          : cpair{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         if constexpr (!PLAIN) v.im = __fmul2_rn(v.im, f2dup(ci));
         return v;
@@ -438,7 +438,7 @@ struct StridedSplitAcc {
             v.re = __fmul2_rn(v.re, f2dup(sx));
             v.im = __fmul2_rn(v.im, f2dup(sy));
         }
-        if (active) SplitPair<S>::store(out + (int64_t)k * stride, v);
+        if (active) SplitPair<S>::template store<SOP>(out + (int64_t)k * stride, v);
     }
     __device__ __forceinline__ int sidx(int k) const { return k * (W / 2) + wp; }
     __device__ __forceinline__ void sstore(int k, cpair v) const {

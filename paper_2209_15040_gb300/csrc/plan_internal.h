@@ -32,7 +32,8 @@ struct PassSpec {
     int twid_shift;              // four-step twiddle: bits of the low table index
     const float2 *tw;            // device stage-twiddle table
     const float2 *tw2;           // fused passes: table of the strided tiles, if it differs
-    // persistent engine passes (kind PASS_ENGINE_A / PASS_ENGINE_B)
+    // persistent engine passes (kind PASS_ENGINE_A / PASS_ENGINE_B, PASS_PERSIST_A,
+    // PASS_WP_A) and the cluster-fused pass A (PASS_SLAB_A: c_scale, s_scale)
     const void *items;           // device item table
     int nitems;
     int64_t units;               // completion counters used (pass A)
@@ -58,11 +59,14 @@ struct Plan {
     cudaStream_t copy_stream = nullptr;  // wsfft_execute_host: copies overlapping the supersteps
     std::vector<cudaEvent_t> pipe_ev;
     int *d_status = nullptr;   // device status word (timeouts)
+    cudaStream_t setup_st = nullptr;  // plan-owned stream for table uploads (synchronised per upload)
+    std::map<cudaStream_t, cudaEvent_t> done_ev;  // per execute stream: recorded after the plan's last launch
     // persistent engine state
     int sm_count = 0;
     int eng_grid = 0;
     int layout = 0;                // wsfft_layout of the spectral side
-    int engine_mode = 0;           // 0 one launch per superstep, 1 persistent, 2 pipelined, 3 warp-per-pencil
+    int engine_mode = 0;           // 0 one launch per superstep, 1 persistent, 2 pipelined, 3 warp-per-pencil,
+                                   // 4 cluster-fused pass A
     int persist_grid = 0;          // persistent kernel blocks (all resident)
     void *d_items = nullptr;       // item tables of passes A and B
     uint32_t *d_ctr = nullptr;     // ticket and completion counters
@@ -90,7 +94,19 @@ struct Plan {
     const float2 *fourstep_table(int64_t L, int shift);
     int build_schedule();
     int build_engine(int64_t n0, int64_t n, bool inv);
+    int build_slab(int64_t n0, int64_t n, bool inv);
+    bool slab_runs(int n);             // cluster-fused pass A resident on this device
+    int slab_checked[2] = {0, 0};      // per slab edge 256 / 512: 0 unknown, 1 yes, -1 no
     int run(const void *in, void *out, cudaStream_t st);
+    // host-to-device copy / zero fill on the plan's own stream, complete on
+    // return (visible to kernels on any stream); a wsfft_status
+    int upload(void *dst, const void *src, size_t bytes);
+    int zero(void *dst, size_t bytes);
+    // remember that the plan's work on `st` ends here (skipped while `st` is
+    // being captured into a graph)
+    void mark_done(cudaStream_t st);
+    // wait for every execute of this plan and its own streams; a wsfft_status
+    int wait_own_work();
     bool can_pipeline_host() const;
     int run_host_pipelined(const void *hin, void *hout, cudaStream_t st);
     // bracket one kernel launch with profiling events (no-op when off)

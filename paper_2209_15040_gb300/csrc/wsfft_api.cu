@@ -28,6 +28,7 @@
 
 #include "../../include/wsfft.h"
 #include "fft_core.cuh"
+#include "host_roots.h"
 #include "pass_desc.h"
 #include "pass_kernels.cuh"
 #include "engine.cuh"
@@ -35,23 +36,11 @@
 #include "plan_internal.h"
 #include "ragged.cuh"
 #include "ragged_desc.h"
+#include "slab_cluster.cuh"
+#include "slab_desc.h"
 
-using namespace wsfft;
+namespace wsfft {
 
-namespace {
-
-bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
-
-int ilog2(int64_t n) {
-    int l = 0;
-    while (((int64_t)1 << l) < n) ++l;
-    return l;
-}
-
-int64_t elem_bytes(int dtype) { return dtype == WSFFT_C32 ? 8 : 4; }
-
-// exp(-2*pi*i*m/n) in long double, reduced to an angle in [0, pi/4] by the
-// eight-fold symmetry of the unit circle, then rounded to float.
 float2 host_root(int64_t m, int64_t n) {
     m %= n;
     if (m < 0) m += n;
@@ -81,16 +70,39 @@ float2 host_root(int64_t m, int64_t n) {
     return make_float2((float)c, (float)-s);
 }
 
-std::vector<float2> stage_table(int N, int E) {
-    std::vector<float2> t((size_t)sched_tw_size(N, E) + 1);
+int fill_stage_table(float2 *dst, int cap, int N, int E) {
+    const int size = sched_tw_size(N, E);
+    if (size + 1 > cap) return -1;
     const int ns = sched_nstages(N, E);
     for (int s = 1; s < ns; ++s) {
         const int R = sched_radix(N, E, s), Ns = sched_ns_before(N, E, s);
         const int off = sched_tw_offset(N, E, s);
         for (int r = 1; r < R; ++r)
-            for (int k = 0; k < Ns; ++k)
-                t[(size_t)off + (size_t)(r - 1) * Ns + k] = host_root((int64_t)r * k, (int64_t)Ns * R);
+            for (int k = 0; k < Ns; ++k) dst[off + (r - 1) * Ns + k] = host_root((int64_t)r * k, (int64_t)Ns * R);
     }
+    dst[size] = make_float2(0.f, 0.f);
+    return size + 1;
+}
+
+}  // namespace wsfft
+
+using namespace wsfft;
+
+namespace {
+
+bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+int ilog2(int64_t n) {
+    int l = 0;
+    while (((int64_t)1 << l) < n) ++l;
+    return l;
+}
+
+int64_t elem_bytes(int dtype) { return dtype == WSFFT_C32 ? 8 : 4; }
+
+std::vector<float2> stage_table(int N, int E) {
+    std::vector<float2> t((size_t)sched_tw_size(N, E) + 1);
+    fill_stage_table(t.data(), (int)t.size(), N, E);
     return t;
 }
 
@@ -166,6 +178,15 @@ cudaError_t launch_wps(int dtype, int n, const WpStridedArgs &b, cudaStream_t st
     }
 }
 
+cudaError_t launch_slab(int dtype, int n, const void *in, void *out, int64_t nslabs, const SlabArgs &a, bool pdl,
+                        cudaStream_t st, int *max_clusters) {
+    switch (dtype) {
+        case WSFFT_C32: return launch_slab_c32(n, in, out, nslabs, a, pdl, st, max_clusters);
+        case WSFFT_C16F: return launch_slab_c16f(n, in, out, nslabs, a, pdl, st, max_clusters);
+        default: return launch_slab_c16bf(n, in, out, nslabs, a, pdl, st, max_clusters);
+    }
+}
+
 cudaError_t launch(int dtype, const PassSpec &p, const void *in, void *out, const PassArgs &a,
                    cudaStream_t st) {
     switch (dtype) {
@@ -189,7 +210,7 @@ const float2 *Plan::tc_table(int N) {
     std::vector<float2> h = tc_table_host(dtype);
     float2 *d = nullptr;
     if (cudaMalloc(&d, h.size() * sizeof(float2)) != cudaSuccess) return nullptr;
-    if (cudaMemcpy(d, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (upload(d, h.data(), h.size() * sizeof(float2)) != WSFFT_SUCCESS) {
         cudaFree(d);
         return nullptr;
     }
@@ -209,7 +230,7 @@ const float2 *Plan::fourstep_table(int64_t L, int shift) {
     for (int64_t j = 0; j < nl; ++j) h[(size_t)(nh + j)] = host_root(j, L);
     float2 *d = nullptr;
     if (cudaMalloc(&d, h.size() * sizeof(float2)) != cudaSuccess) return nullptr;
-    if (cudaMemcpy(d, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (upload(d, h.data(), h.size() * sizeof(float2)) != WSFFT_SUCCESS) {
         cudaFree(d);
         return nullptr;
     }
@@ -224,7 +245,7 @@ const float2 *Plan::table(int N, int E) {
     std::vector<float2> h = stage_table(N, E);
     float2 *d = nullptr;
     if (cudaMalloc(&d, h.size() * sizeof(float2)) != cudaSuccess) return nullptr;
-    if (cudaMemcpy(d, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (upload(d, h.data(), h.size() * sizeof(float2)) != WSFFT_SUCCESS) {
         cudaFree(d);
         return nullptr;
     }
@@ -289,9 +310,7 @@ int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
         d_items = nullptr;
         return WSFFT_ERR_ALLOC;
     }
-    if (cudaMemcpy(d_items, items.data(), items.size() * sizeof(EngItem), cudaMemcpyHostToDevice) !=
-        cudaSuccess)
-        return WSFFT_ERR_CUDA;
+    if (upload(d_items, items.data(), items.size() * sizeof(EngItem)) != WSFFT_SUCCESS) return WSFFT_ERR_CUDA;
     if (1 + U > ctr_cap) {
         if (d_ctr) cudaFree(d_ctr);
         d_ctr = nullptr;
@@ -369,6 +388,81 @@ int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
     return WSFFT_SUCCESS;
 }
 
+// Whether the cluster-fused pass A of slab edge n can be resident on this
+// plan's device (asked once per edge).
+bool Plan::slab_runs(int n) {
+    if (!slab_supports(n)) return false;
+    int &c = slab_checked[n == 512 ? 1 : 0];
+    if (c == 0) {
+        SlabArgs probe{};
+        int clusters = 0;
+        const cudaError_t e = launch_slab(dtype, n, nullptr, nullptr, 1, probe, false, 0, &clusters);
+        cudaGetLastError();  // a refused query leaves no sticky error
+        c = (e == cudaSuccess && clusters > 0) ? 1 : -1;
+    }
+    return c > 0;
+}
+
+// Two-trip schedule of an n0 x n x n transform with the cluster-fused pass A
+// (slab_cluster.cuh): the z and y supersteps of each n x n slab in one
+// thread-block cluster (in -> out), then the x superstep as one launch of the
+// strided kernel (out, in place).
+int Plan::build_slab(int64_t n0, int64_t n, bool inv) {
+    PassSpec a{};
+    a.kind = PASS_SLAB_A;
+    a.N = (int)n;
+    a.inner = 1;
+    a.npencils_per_batch = n0 * n;  // z pencils per transform
+    a.units = n0;                   // slabs per transform
+    a.transform_elems = n0 * n * n;
+    a.src = SRC_IN;
+    a.dst = DST_OUT;
+    a.conj_in = inv;
+    PassSpec b{};
+    b.kind = PASS_STRIDED;
+    b.N = (int)n0;
+    b.E = default_E((int)n0);
+    b.tile = 0;
+    if (n0 == 512) {
+        // the shape of the x superstep in the one-launch-per-superstep
+        // schedule: 32 values per thread in complex64, split-form pencil
+        // pairs in the 16-bit types
+        b.E = dtype == WSFFT_C32 ? 32 : 16;
+        b.tile = dtype == WSFFT_C32 ? 16 : SPLIT_TILE + 16;
+    } else if (n0 == 1024) {
+        b.E = 32;
+        b.tile = 16;
+    }
+    b.inner = n * n;
+    b.npencils_per_batch = n * n;
+    b.transform_elems = n0 * n * n;
+    b.src = SRC_OUT;
+    b.dst = DST_OUT;
+    b.conj_out = inv;
+    const float sc = axis_scale(n, dir, norm), sc0 = axis_scale(n0, dir, norm);
+    if (dtype == WSFFT_C32 && norm != WSFFT_NORM_ORTHO) {
+        // complex64 defers every superstep's scale to the last store
+        a.c_scale = a.s_scale = 1.f;
+        b.scale = (float)((double)sc * (double)sc * (double)sc0);
+    } else {
+        a.c_scale = a.s_scale = sc;
+        b.scale = sc0;
+    }
+    passes.push_back(a);
+    passes.push_back(b);
+    for (auto &kv : overrides)
+        if (kv.first == 1) {
+            passes[1].E = kv.second.first;
+            passes[1].tile = kv.second.second;
+        }
+    passes[0].E = slab_ez(dtype != WSFFT_C32);
+    passes[0].tw = table((int)n, passes[0].E);
+    passes[0].tw2 = table((int)n, slab_ey());
+    passes[1].tw = table(passes[1].N, passes[1].E);
+    if (!passes[0].tw || !passes[0].tw2 || !passes[1].tw) return WSFFT_ERR_ALLOC;
+    return WSFFT_SUCCESS;
+}
+
 // (Re)build the pass list from shape, direction and normalisation.
 int Plan::build_schedule() {
     passes.clear();
@@ -422,9 +516,14 @@ int Plan::build_schedule() {
         }
     };
 
+    // cluster-fused pass A (the default): the two inner axes equal and built
+    // for that edge, and the kernel resident on this device
+    if (layout == WSFFT_LAYOUT_NATURAL && r == 3 && engine_mode == 4 && d[1] == d[2] && slab_runs((int)d[1]))
+        return build_slab(d[0], d[1], inv);
     // fused schedules: the two inner axes equal (n x n slabs); the pipelined
     // engine also runs the outer axis, so it needs a cube
-    if (layout == WSFFT_LAYOUT_NATURAL && r == 3 && engine_mode != 0 && d[1] == d[2] && engine_supports((int)d[1]) &&
+    if (layout == WSFFT_LAYOUT_NATURAL && r == 3 && engine_mode >= 1 && engine_mode <= 3 && d[1] == d[2] &&
+        engine_supports((int)d[1]) &&
         (engine_mode != 2 || d[0] == d[1]) && (engine_mode != 3 || wp_supports((int)d[1])) &&
         eng_grid > 0) {
         return build_engine(d[0], d[1], inv);
@@ -650,6 +749,23 @@ int Plan::run(const void *in, void *out, cudaStream_t st) {
                 if (err != cudaSuccess) return err == cudaErrorInvalidValue ? WSFFT_ERR_UNSUPPORTED : WSFFT_ERR_CUDA;
                 continue;
             }
+            if (p.kind == PASS_SLAB_A) {
+                const int64_t off = b0 * p.transform_elems * eb;
+                SlabArgs sa{};
+                sa.ci = p.conj_in ? -1.f : 1.f;
+                sa.zsx = sa.zsy = p.c_scale;
+                sa.ysx = sa.ysy = p.s_scale;
+                sa.tw_z = p.tw;
+                sa.tw_y = p.tw2;
+                const int64_t nslabs = p.units * nb;
+                const bool pdl = !p.no_pdl && nslabs * (int64_t)p.N * p.N * eb <= ((int64_t)2 << 30);
+                prof_begin(st);
+                cudaError_t e = launch_slab(dtype, p.N, (const char *)in + off, (char *)out + off, nslabs, sa, pdl,
+                                            st, nullptr);
+                prof_end(st);
+                if (e != cudaSuccess) return e == cudaErrorInvalidValue ? WSFFT_ERR_UNSUPPORTED : WSFFT_ERR_CUDA;
+                continue;
+            }
             if (p.kind == PASS_ENGINE_A || p.kind == PASS_ENGINE_B || p.kind == PASS_PERSIST_A ||
                 p.kind == PASS_WP_A) {
                 EngArgs e{};
@@ -818,6 +934,48 @@ int Plan::run_host_pipelined(const void *hin, void *hout, cudaStream_t st) {
     return WSFFT_SUCCESS;
 }
 
+int Plan::upload(void *dst, const void *src, size_t bytes) {
+    if (!setup_st && cudaStreamCreateWithFlags(&setup_st, cudaStreamNonBlocking) != cudaSuccess) {
+        setup_st = nullptr;
+        return WSFFT_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, setup_st) != cudaSuccess) return WSFFT_ERR_CUDA;
+    return cudaStreamSynchronize(setup_st) == cudaSuccess ? WSFFT_SUCCESS : WSFFT_ERR_CUDA;
+}
+
+int Plan::zero(void *dst, size_t bytes) {
+    if (!setup_st && cudaStreamCreateWithFlags(&setup_st, cudaStreamNonBlocking) != cudaSuccess) {
+        setup_st = nullptr;
+        return WSFFT_ERR_CUDA;
+    }
+    if (cudaMemsetAsync(dst, 0, bytes, setup_st) != cudaSuccess) return WSFFT_ERR_CUDA;
+    return cudaStreamSynchronize(setup_st) == cudaSuccess ? WSFFT_SUCCESS : WSFFT_ERR_CUDA;
+}
+
+void Plan::mark_done(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return;  // a graph's launches are the caller's to wait for
+    auto it = done_ev.find(st);
+    if (it == done_ev.end()) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return;
+        it = done_ev.emplace(st, e).first;
+    }
+    cudaEventRecord(it->second, st);
+}
+
+int Plan::wait_own_work() {
+    bool ok = true;
+    for (auto &kv : done_ev) ok &= cudaEventSynchronize(kv.second) == cudaSuccess;
+    if (copy_stream) ok &= cudaStreamSynchronize(copy_stream) == cudaSuccess;
+    if (setup_st) ok &= cudaStreamSynchronize(setup_st) == cudaSuccess;
+    return ok ? WSFFT_SUCCESS : WSFFT_ERR_CUDA;
+}
+
 void Plan::prof_begin(cudaStream_t st) {
     if (prof_used < (int)prof_ev.size() / 2) cudaEventRecord(prof_ev[2 * prof_used], st);
 }
@@ -844,6 +1002,8 @@ Plan::~Plan() {
     for (auto e : pipe_ev) cudaEventDestroy(e);
     if (copy_stream) cudaStreamDestroy(copy_stream);
     if (d_status) cudaFree(d_status);
+    for (auto &kv : done_ev) cudaEventDestroy(kv.second);
+    if (setup_st) cudaStreamDestroy(setup_st);
 }
 
 }  // namespace wsfft
@@ -885,10 +1045,6 @@ int wsfft_plan_create(wsfft_plan *plan, const int64_t *dims, int rank, int dtype
     for (int i = 0; i < rank; ++i) p->dims[i] = dims[i];
     cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
     p->eng_grid = p->sm_count;  // one engine block per SM (its shared memory fills the SM)
-    {
-        const char *env = getenv("WSFFT_ENGINE");
-        if (env && env[0] >= '0' && env[0] <= '3') p->engine_mode = env[0] - '0';
-    }
     p->dtype = dtype;
     p->dir = direction;
     p->batch = batch;
@@ -900,17 +1056,16 @@ int wsfft_plan_create(wsfft_plan *plan, const int64_t *dims, int rank, int dtype
         delete p;
         return WSFFT_ERR_ALLOC;
     }
-    cudaMemset(p->d_status, 0, sizeof(int));
+    if (p->zero(p->d_status, sizeof(int)) != WSFFT_SUCCESS) {
+        delete p;
+        return WSFFT_ERR_CUDA;
+    }
     int rc = p->build_schedule();
     if (rc != WSFFT_SUCCESS) {
         delete p;
         return rc;
     }
     autotune_apply_cached(*p);  // a remembered choice for this key, if any
-    if (cudaDeviceSynchronize() != cudaSuccess) {
-        delete p;
-        return WSFFT_ERR_CUDA;
-    }
     *plan = reinterpret_cast<wsfft_plan>(p);
     return WSFFT_SUCCESS;
 }
@@ -952,7 +1107,9 @@ int wsfft_execute(wsfft_plan plan, const void *in, void *out, wsfft_stream strea
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || p->ragged || !in || !out) return WSFFT_ERR_INVALID_ARG;
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return WSFFT_ERR_INVALID_ARG;
-    return p->run(in, out, (cudaStream_t)stream);
+    const int rc = p->run(in, out, (cudaStream_t)stream);
+    p->mark_done((cudaStream_t)stream);
+    return rc;
 }
 
 int wsfft_execute_host(wsfft_plan plan, const void *host_in, void *host_out, wsfft_stream stream) {
@@ -971,6 +1128,28 @@ int wsfft_execute_host(wsfft_plan plan, const void *host_in, void *host_out, wsf
         if (rc != WSFFT_SUCCESS) return rc;
         return cuda_status(cudaStreamSynchronize(st));
     }
+    if (!p->passes.empty() && p->passes[0].kind == PASS_SLAB_A) {
+        // The host pipeline overlaps the copies with the three one-launch
+        // supersteps (the slab-local z and y hide behind the chunked
+        // copies); the fused pass A would leave the copy back unoverlapped.
+        // Use that schedule for this call, then restore the plan's own.
+        const int mode = p->engine_mode;
+        const auto over = p->overrides;
+        p->engine_mode = 0;
+        p->overrides.clear();
+        int rc = p->build_schedule();
+        const bool ok = rc == WSFFT_SUCCESS && p->can_pipeline_host();
+        if (ok) rc = p->run_host_pipelined(host_in, host_out, st);
+        p->engine_mode = mode;
+        p->overrides = over;
+        const int rc2 = p->build_schedule();
+        if (ok) {
+            if (rc != WSFFT_SUCCESS) return rc;
+            if (rc2 != WSFFT_SUCCESS) return rc2;
+            return cuda_status(cudaStreamSynchronize(st));
+        }
+        if (rc2 != WSFFT_SUCCESS) return rc2;
+    }
     if (cudaMemcpyAsync(p->host_buf, host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return WSFFT_ERR_CUDA;
     int rc = p->run(p->host_buf, p->host_buf, st);
@@ -987,10 +1166,10 @@ int wsfft_destroy(wsfft_plan plan) {
     const int dev = p->device;
     cudaGetDevice(&prev);
     if (prev != dev) cudaSetDevice(dev);
-    cudaError_t e = cudaDeviceSynchronize();
+    const int rc = p->wait_own_work();  // this plan's executes only, not the whole device
     delete p;
     if (prev >= 0 && prev != dev) cudaSetDevice(prev);
-    return cuda_status(e);
+    return rc;
 }
 
 int wsfft_plan_set_pass_variant(wsfft_plan plan, int pass, int values_per_thread, int tile) {
@@ -1017,7 +1196,8 @@ int wsfft_plan_set_pass_variant(wsfft_plan plan, int pass, int values_per_thread
 
 int wsfft_plan_set_engine(wsfft_plan plan, int mode) {
     Plan *p = reinterpret_cast<Plan *>(plan);
-    if (!p || mode < 0 || mode > 3) return WSFFT_ERR_INVALID_ARG;
+    if (!p || mode < 0 || mode > 4) return WSFFT_ERR_INVALID_ARG;
+    if (p->ragged) return WSFFT_ERR_UNSUPPORTED;
     p->engine_mode = mode;
     return p->build_schedule();
 }
@@ -1038,11 +1218,13 @@ int wsfft_plan_sync_status(wsfft_plan plan, wsfft_stream stream) {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p) return WSFFT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return WSFFT_ERR_CUDA;
     int h = 0;
-    if (cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpyAsync(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
         return WSFFT_ERR_CUDA;
-    if (h != 0) cudaMemset(p->d_status, 0, sizeof(int));
+    if (h != 0 && (cudaMemsetAsync(p->d_status, 0, sizeof(int), st) != cudaSuccess ||
+                   cudaStreamSynchronize(st) != cudaSuccess))
+        return WSFFT_ERR_CUDA;
     return h == 0 ? WSFFT_SUCCESS : WSFFT_ERR_DEVICE_TIMEOUT;
 }
 
@@ -1112,7 +1294,7 @@ int wsfft_plan_create_ragged(wsfft_plan *plan, int count, const int64_t *dims, i
         p->d_status = nullptr;
         return fail(WSFFT_ERR_ALLOC);
     }
-    cudaMemset(p->d_status, 0, sizeof(int));
+    if (p->zero(p->d_status, sizeof(int)) != WSFFT_SUCCESS) return fail(WSFFT_ERR_CUDA);
     std::vector<RagInst> inst((size_t)count);
     for (int i = 0; i < count; ++i) {
         RagInst &I = inst[i];
@@ -1165,7 +1347,7 @@ int wsfft_plan_create_ragged(wsfft_plan *plan, int count, const int64_t *dims, i
         return fail(WSFFT_ERR_ALLOC);
     }
     memcpy(p->rag_inst_host, inst.data(), nb);
-    if (cudaMemcpy(p->rag_items, items.data(), ib, cudaMemcpyHostToDevice) != cudaSuccess) return fail(WSFFT_ERR_CUDA);
+    if (p->upload(p->rag_items, items.data(), ib) != WSFFT_SUCCESS) return fail(WSFFT_ERR_CUDA);
     if (cudaMalloc(&p->d_ctr, (size_t)(1 + 2 * count) * sizeof(uint32_t)) != cudaSuccess) {
         p->d_ctr = nullptr;
         return fail(WSFFT_ERR_ALLOC);
@@ -1182,7 +1364,6 @@ int wsfft_plan_create_ragged(wsfft_plan *plan, int count, const int64_t *dims, i
                                           : launch_ragged_c16bf(dummy, &per_sm, 0, 0);
     if (e != cudaSuccess || per_sm < 1) return fail(WSFFT_ERR_CUDA);
     p->rag_grid = per_sm * p->sm_count;
-    if (cudaDeviceSynchronize() != cudaSuccess) return fail(WSFFT_ERR_CUDA);
     *plan = reinterpret_cast<wsfft_plan>(p);
     return WSFFT_SUCCESS;
 }
@@ -1228,6 +1409,7 @@ int wsfft_execute_ragged(wsfft_plan plan, const void *const *in, void *const *ou
                     : p->dtype == WSFFT_C16F ? launch_ragged_c16f(a, nullptr, p->rag_grid, st)
                                              : launch_ragged_c16bf(a, nullptr, p->rag_grid, st);
     p->prof_end(st);
+    p->mark_done(st);
     return e == cudaSuccess ? WSFFT_SUCCESS : WSFFT_ERR_CUDA;
 }
 

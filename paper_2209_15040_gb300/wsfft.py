@@ -163,8 +163,9 @@ class Plan:
                                                  int(tile)), "wsfft_plan_set_pass_variant")
 
     def set_engine(self, mode) -> None:
-        """Cube schedule: 0 one launch per superstep (default), 3 warp-per-pencil,
-        1 persistent, 2 pipelined."""
+        """Schedule of an n0 x n x n transform: 4 cluster-fused z and y per slab
+        (the default where it is built: n in {256, 512}), 0 one launch per
+        superstep, 3 warp-per-pencil, 1 persistent, 2 pipelined."""
         _check(lib().wsfft_plan_set_engine(self._h, int(mode)), "wsfft_plan_set_engine")
 
     def set_wait_test(self, withhold: bool, timeout_ns: int) -> None:

@@ -1,7 +1,9 @@
 """GPU parity of the n^3 cube schedules -- one launch per superstep (the
 default) and the two-launch schedules that fuse the supersteps along the two
-inner axes per slab through L2 -- at sizes up to the 512^3 benchmark
-configuration, plus the bounded-wait failure path of the fused schedules."""
+inner axes per slab (through L2: per thread-block cluster with a cluster
+barrier, or in persistent kernels with per-slab counters) -- at sizes up to
+the 512^3 benchmark configuration, plus the bounded-wait failure path of the
+persistent schedules."""
 import numpy as np
 import pytest
 import torch
@@ -53,7 +55,7 @@ def test_engine_matches_superstep_schedule(n):
     x = to_device(xs, "c32")
     ref = oracle.fftn(xs.astype(np.complex128), rank=3)
     outs = {}
-    for mode, want in ((3, 2), (1, 2), (2, 2), (0, 3)):
+    for mode, want in ((4, 2 if n == 512 else 3), (3, 2), (1, 2), (2, 2), (0, 3)):
         y, npass = run(x, (n, n, n), "c32", W.FORWARD, batch=batch, engine=mode)
         assert npass == want
         outs[mode] = to_host_c128(y, "c32")
@@ -85,9 +87,11 @@ def test_engine_half_storage(dtype, n, mode):
 
 # -- the benchmark configuration at full size ----------------------------------
 
-@pytest.mark.parametrize("direction,mode", [(W.FORWARD, None), (W.INVERSE, None), (W.FORWARD, 3)])
+@pytest.mark.parametrize("direction,mode", [(W.FORWARD, None), (W.INVERSE, None), (W.FORWARD, 4), (W.INVERSE, 4),
+                                            (W.FORWARD, 3)])
 def test_512cubed_full_size(direction, mode):
-    # mode None: the plan's default schedule, the one bench.py times
+    # mode None: the plan's default schedule (one launch per superstep), the
+    # one bench.py times; 4: the cluster-fused pass A; 3: warp-per-pencil
     n = 512
     xs, xc = seeded((n, n, n), 1, "normal", "c32")
     y, npass = run(to_device(xs, "c32"), (n, n, n), "c32", direction, engine=mode)
@@ -178,10 +182,45 @@ def test_1024cubed_forward_sampled():
     inv.close()
 
 
-@pytest.mark.parametrize("mode", [1, 3])
+@pytest.mark.parametrize("mode", [1, 3, 4])
 @pytest.mark.parametrize("shape", [(64, 512, 512), (32, 128, 128), (256, 256, 256), (2, 512, 512)])
 def test_fused_schedule_any_outer_axis(mode, shape):
     xs, xc = seeded(shape, 12, "normal", "c32")
     y, npass = run(to_device(xs, "c32"), shape, "c32", W.FORWARD, engine=mode)
-    assert npass == 2
+    # the cluster-fused pass A is built for slab edges 256 and 512 only;
+    # other edges fall back to one launch per superstep
+    assert npass == (3 if mode == 4 and shape[1] == 128 else 2)
     assert oracle.rel_l2(to_host_c128(y, "c32"), oracle.fftn(xc)) < TOL["c32"]
+
+
+# -- the cluster-fused pass A (schedule 4, slab edges 256 and 512) -------------------
+
+@pytest.mark.parametrize("dtype", ["c32", "c16f", "c16bf"])
+@pytest.mark.parametrize("direction", [W.FORWARD, W.INVERSE])
+@pytest.mark.parametrize("shape,batch", [((256, 256, 256), 1), ((4, 512, 512), 3), ((2, 256, 256), 2)])
+def test_cluster_pass_a(dtype, direction, shape, batch):
+    dist = "normal" if dtype == "c32" else "uniform"
+    xs, xc = seeded((batch,) + shape, 21, dist, dtype)
+    y, npass = run(to_device(xs, dtype), shape, dtype, direction, batch=batch, engine=4)
+    assert npass == 2
+    norm = oracle.NORM_PAPER if dtype == "c32" else oracle.NORM_ORTHO
+    ref = oracle.fftn(xc, rank=3, sign=direction, norm=norm)
+    err = oracle.rel_l2(to_host_c128(y, dtype), ref)
+    print(f"cluster pass A {shape} x{batch} {dtype} dir {direction}: rel_l2 {err:.3e}")
+    assert err < TOL[dtype]
+
+
+@pytest.mark.parametrize("norm", [W.NORM_NONE, W.NORM_ORTHO, W.NORM_FORWARD])
+def test_cluster_pass_a_norms_in_place(norm):
+    shape = (8, 512, 512)
+    xs, xc = seeded(shape, 22, "normal", "c32")
+    for direction in (W.FORWARD, W.INVERSE):
+        y, npass = run(to_device(xs, "c32"), shape, "c32", direction, norm=norm, inplace=True, engine=4)
+        assert npass == 2
+        if norm == W.NORM_FORWARD:
+            # the oracle has no forward-scaled mode: forward / N, inverse unscaled
+            sc = 1.0 / (512 * 512 * 8) if direction == W.FORWARD else 1.0
+            ref = sc * oracle.fftn(xc, sign=direction, norm=oracle.NORM_NONE)
+        else:
+            ref = oracle.fftn(xc, sign=direction, norm=norm)
+        assert oracle.rel_l2(to_host_c128(y, "c32"), ref) < TOL["c32"]
