@@ -134,7 +134,7 @@ class Clocks:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.ident, f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -172,57 +172,58 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_sample_oracle(reps: int = 2):
-    """FP64 CPU oracle on a bounded sample: `reps` forward+inverse pairs of a
-    256^3 transform, scaled to a 512^3 transform by the 5 N log2 N count."""
+def oracle_pair(x):
+    """One FP64 forward + inverse pair of the oracle on x; seconds."""
     import oracle
+    t0 = time.perf_counter()
+    y = oracle.fftn(x, sign=-1)
+    oracle.fftn(y, sign=+1)
+    return time.perf_counter() - t0
+
+
+def oracle_input(n=N_AXIS):
     from paper_2209_15040_gb300 import inputs
+    return inputs.complex_input((n, n, n), 1, "normal", "c32").astype(np.complex128)
+
+
+def cpu_sample_oracle(reps: int = 3):
+    """FP64 CPU oracle at the benchmark size: `reps` forward+inverse pairs of
+    the 512^3 transform (about 1-2 s each on 16 cores), median per transform."""
+    import oracle
     cores = len(os.sched_getaffinity(0))
     oracle.set_threads(cores)
-    n = 256
-    x = inputs.complex_input((n, n, n), 1, "normal", "c32").astype(np.complex128)
-    best = float("inf")
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        y = oracle.fftn(x, sign=-1)
-        oracle.fftn(y, sign=+1)
-        best = min(best, time.perf_counter() - t0)
-    small_flops = 5.0 * n ** 3 * math.log2(n ** 3)
-    us = best / 2 * (FLOPS / small_flops) * 1e6
-    return {"value": us, "unit": "us per 512^3 transform", "cores": oracle.get_threads(),
+    x = oracle_input()
+    times = [oracle_pair(x) for _ in range(reps)]
+    us = statistics.median(times) / 2 * 1e6
+    return {"value": round(us, 1), "unit": "us per 512^3 transform", "cores": oracle.get_threads(),
             "kind": "oracle",
-            "sample": f"best of {reps} FP64 forward+inverse pairs at 256^3, "
-                      f"/2 and scaled by 5N log2 N to 512^3"}
+            "sample": f"median of {reps} FP64 forward+inverse pairs at 512^3 (the benchmark size), /2"}
 
 
 def run_reference(args, world, rank):
-    """The oracle as it stands, on host cores: the reference arm."""
+    """The oracle as it stands, on host cores: the reference arm.  Each step
+    is one FP64 forward + inverse pair at 512^3, the benchmark's own
+    workload (no scaling)."""
     if rank != 0:
         return
     import oracle
-    from paper_2209_15040_gb300 import inputs
     cores = len(os.sched_getaffinity(0))
     oracle.set_threads(cores)
-    n = 128
-    x = inputs.complex_input((n, n, n), 1, "normal", "c32").astype(np.complex128)
-    scale = FLOPS / (5.0 * n ** 3 * math.log2(n ** 3))
+    n = args.ref_n
+    x = oracle_input(n)
     for _ in range(args.warmup):
-        oracle.fftn(oracle.fftn(x, sign=-1), sign=+1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.fftn(oracle.fftn(x, sign=-1), sign=+1)
-    dt = time.perf_counter() - t0
-    us = dt / args.steps / 2 * scale * 1e6
-    line = {"metric": METRIC, "value": us, "unit": "us", "n_gpus": args.gpus,
+        oracle_pair(x)
+    dt = sum(oracle_pair(x) for _ in range(args.steps))
+    us = dt / args.steps / 2 * 1e6
+    line = {"metric": METRIC, "value": round(us, 1), "unit": "us", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "l2": "input larger than L2"},
-            "cpu_baseline": {"value": us, "unit": "us", "cores": oracle.get_threads(),
+            "config": {"workload": WORKLOAD, "dims": [n, n, n], "l2": "input larger than L2"},
+            "cpu_baseline": {"value": round(us, 1), "unit": "us", "cores": oracle.get_threads(),
                              "kind": "oracle",
-                             "sample": f"each step one FP64 forward+inverse pair at {n}^3, "
-                                       f"/2 and scaled by 5N log2 N to 512^3"},
-            "e2e": {"value": us, "unit": "us", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                             "sample": f"each step one FP64 forward+inverse pair at {n}^3, /2"},
+            "e2e": {"value": round(us, 1), "unit": "us", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -434,12 +435,15 @@ def run_case(args):
         x = torch.randn(dims + (2,), device="cuda").to(torch.float16 if code == W.C16F else torch.bfloat16)
     y = torch.empty_like(x)
     plan = W.Plan(dims, code, W.FORWARD, 1)
+    if args.case_engine is not None:
+        plan.set_engine(args.case_engine)
     if args.case_variant:
         plan.set_pass_variant(*(int(v) for v in args.case_variant.split(",")))
     for _ in range(args.case_reps):
         plan.execute(x.data_ptr(), y.data_ptr())
     torch.cuda.synchronize()
     print(json.dumps({"case": list(dims), "dtype": args.case_dtype, "variant": args.case_variant,
+                      "engine": args.case_engine,
                       "passes": plan.passes()[0], "reps": args.case_reps, "status": plan.sync_status()}))
     plan.close()
 
@@ -471,6 +475,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wsfft", choices=["wsfft", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--ref-n", type=int, default=N_AXIS,
+                    help="reference arm: cube edge of its transforms (default: the benchmark's 512; "
+                         "smaller only for tests of the launch path)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch leg")
     ap.add_argument("--no-sizes", action="store_true", help="skip the other-sizes leg")
@@ -480,6 +487,8 @@ def main():
                          "--case-reps times (forward, N(0,1) input, storage --case-dtype) and exit")
     ap.add_argument("--case-reps", type=int, default=3)
     ap.add_argument("--case-dtype", default="c32", choices=["c32", "c16f", "c16bf"])
+    ap.add_argument("--case-engine", type=int, default=None,
+                    help="schedule of the case's plan (wsfft_plan_set_engine: 0..4)")
     ap.add_argument("--case-variant", default=None,
                     help="PASS,E,TILE: kernel shape of one pass (wsfft_plan_set_pass_variant)")
     ap.add_argument("--sweep", action="store_true",
@@ -552,8 +561,14 @@ def main():
         pass_ms[i % npass].append(t)
     mean_ms = [statistics.mean(v) if v else 0.0 for v in pass_ms]
     dom = int(np.argmax(mean_ms))
-    bytes_launch = 2 * ELEMS * 8  # one read and one write of the array
+    # algorithmic bytes of one launch: its share of the minimum-bytes
+    # roofline of a transform (2 passes x read + write of the 1 GiB array,
+    # whatever the schedule), i.e. 4 GiB / launches per transform
+    min_bytes = REF_PASSES * 2 * ELEMS * 8
+    bytes_launch = min_bytes / npass
     achieved = bytes_launch / (mean_ms[dom] * 1e-3) / 1e9
+    # the launch's own read + write of the whole array (what it moves)
+    io_launch = 2 * ELEMS * 8
     traffic = kernel_traffic(dom)
 
     # --- FP16 / BF16 storage, same step
@@ -639,7 +654,6 @@ def main():
         cpu = cpu_sample_oracle()
 
     if rank == 0:
-        min_bytes = REF_PASSES * 2 * ELEMS * 8
         line = {
             "metric": METRIC, "value": round(us_per_transform, 2), "unit": "us",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -662,7 +676,12 @@ def main():
                          "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                          "traffic": traffic, "kernel": f"pass {dom} of {npass}",
                          "per_pass_ms": [round(v, 4) for v in mean_ms],
-                         "bytes_per_launch": bytes_launch, "peak_kind": peak_kind},
+                         "bytes_per_launch": int(bytes_launch),
+                         "bytes_per_launch_note": "2-pass minimum bytes of a transform / launches per transform",
+                         "io_bytes_per_launch": io_launch,
+                         "io_gbs": round(io_launch / (mean_ms[dom] * 1e-3) / 1e9, 1),
+                         "io_frac": round(io_launch / (mean_ms[dom] * 1e-3) / 1e9 / hbm_peak, 4),
+                         "peak_kind": peak_kind},
             "rel_l2_roundtrip_c32": rt32,
             "max_abs_roundtrip_c32": rt32_max_abs,
             "device": device_info(dev),

@@ -59,7 +59,7 @@ def test_reference_arm_under_torchrun_world_size_2():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
-           "--gpus", "2", "--steps", "1", "--warmup", "3"]
+           "--gpus", "2", "--steps", "1", "--warmup", "3", "--ref-n", "64"]
     env = dict(os.environ)
     env["CUDA_VISIBLE_DEVICES"] = ""
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
