@@ -1,7 +1,7 @@
 """GPU parity of the ragged batch: uneven 3D shapes in one persistent launch
 (the ragged configuration: 256 shapes with axes drawn from {32, 64, 128, 256}
-by seed 4), against the FP64 oracle and against one plan per instance, plus
-replay under a captured CUDA graph."""
+by seed 4), every instance against the FP64 oracle, in every storage type,
+plus replay under a captured CUDA graph."""
 import numpy as np
 import pytest
 import torch
@@ -56,8 +56,8 @@ def test_ragged_in_place():
 
 def test_ragged_256_shapes_seed4():
     # the full ragged configuration; data generated on the device (seeded per
-    # instance), every instance checked against its own plan, every 8th
-    # against the FP64 oracle
+    # instance), every instance checked element by element against the FP64
+    # oracle
     shapes = inputs.ragged_shapes(256, 4)
     g = torch.Generator(device="cuda")
     xd, outs = [], []
@@ -70,19 +70,33 @@ def test_ragged_256_shapes_seed4():
     plan.execute([x.data_ptr() for x in xd], [y.data_ptr() for y in outs])
     torch.cuda.synchronize()
     assert plan.sync_status() == W.SUCCESS
+    plan.close()
     worst = 0.0
-    for i, (s, x, y) in enumerate(zip(shapes, xd, outs)):
-        p1 = W.Plan(tuple(int(v) for v in s), W.C32, W.FORWARD, 1)
-        r = torch.empty_like(x)
-        p1.execute(x.data_ptr(), r.data_ptr())
-        torch.cuda.synchronize()
-        worst = max(worst, oracle.rel_l2(y.cpu().numpy(), r.cpu().numpy()))
-        p1.close()
-        if i % 8 == 0:
-            ref = oracle.fftn(x.cpu().numpy().astype(np.complex128))
-            assert oracle.rel_l2(y.cpu().numpy(), ref) < TOL["c32"], i
-    print(f"ragged 256 vs per-instance plans: worst rel_l2 {worst:.2e}")
-    assert worst < TOL["c32"]
+    for i, (x, y) in enumerate(zip(xd, outs)):
+        ref = oracle.fftn(x.cpu().numpy().astype(np.complex128))
+        err = oracle.rel_l2(y.cpu().numpy(), ref)
+        worst = max(worst, err)
+        assert err < TOL["c32"], (i, shapes[i], err)
+    print(f"ragged 256 vs oracle: worst rel_l2 {worst:.2e}")
+
+
+@pytest.mark.parametrize("dtype", ["c16f", "c16bf"])
+@pytest.mark.parametrize("direction", [W.FORWARD, W.INVERSE])
+def test_ragged_half_storage_256_axes(dtype, direction):
+    # 16-bit storage with 256-point axes in every position (the longest
+    # ragged axis), against the oracle under the orthonormal scaling
+    shapes = np.array([[256, 32, 64], [32, 256, 128], [64, 128, 256], [256, 256, 32], [32, 64, 256]])
+    xs, xd = make_inputs(shapes, dtype, 400)
+    outs = [torch.empty_like(x) for x in xd]
+    plan = W.RaggedPlan(shapes, DT[dtype], direction)
+    plan.execute([x.data_ptr() for x in xd], [y.data_ptr() for y in outs])
+    torch.cuda.synchronize()
+    assert plan.sync_status() == W.SUCCESS
+    for s, x, y in zip(shapes, xs, outs):
+        ref = oracle.fftn(inputs.storage_to_c128(x, dtype), sign=direction, norm=oracle.NORM_ORTHO)
+        err = oracle.rel_l2(to_host_c128(y, dtype), ref)
+        print(f"ragged {dtype} {tuple(s)} dir {direction}: rel_l2 {err:.2e}")
+        assert err < TOL[dtype]
     plan.close()
 
 
