@@ -122,6 +122,38 @@ typedef enum {
 int wsfft_plan_create(wsfft_plan *plan, const int64_t *dims, int rank, int dtype,
                       int direction, int64_t batch);
 
+/* Create a plan for one superstep: `batch` x `inner` independent 1D
+ * transforms of length n along an axis whose consecutive elements are
+ * `inner` elements apart -- the array is [batch][n][inner] (row-major) and
+ * pencil (b, i) is its elements (b, 0..n-1, i).  inner = 1 is a batch of
+ * contiguous transforms.  This is the superstep of Section 4.1 on its own,
+ * for arrays whose other axes are transformed elsewhere (the x superstep of
+ * a slab-distributed 3D transform runs on each GPU's y-slab with it).
+ *   n: power of two, 2..4096; inner: power of two >= 1; batch >= 1.
+ * Normalisation: scale 1/n on the inverse under WSFFT_NORM_PAPER (the
+ * default for WSFFT_C32), 1/sqrt(n) both ways under WSFFT_NORM_ORTHO (the
+ * default for the 16-bit types); wsfft_plan_set_norm changes it.  Layouts
+ * other than natural return UNSUPPORTED.  Executes through wsfft_execute /
+ * wsfft_execute_host like any plan.
+ * Errors: INVALID_ARG, INVALID_SIZE, ALLOC, CUDA. */
+int wsfft_plan_create_axis(wsfft_plan *plan, int64_t n, int64_t inner, int dtype,
+                           int direction, int64_t batch);
+
+/* out[b][a][c] = in[a][b][c] for a < A, b < B, c < C elements of `dtype`:
+ * swap the two outer axes of a row-major [A][B][C] array, moving each run of
+ * C elements whole.  The redistribution of a slab-distributed transform
+ * (Section 2.1, data distribution; Section 4.3, redistribution between
+ * supersteps): before an all-to-all a rank's [rows][destination][share]
+ * becomes [destination][rows][share], one contiguous send block per rank,
+ * and after the inverse's all-to-all the received [source][rows][share]
+ * goes back to row order.  in and out: device pointers, must not overlap;
+ * asynchronous on `stream`.  Moves 16-byte vectors when C's byte length and
+ * both pointers are multiples of 16.
+ * Errors: INVALID_ARG (null, overlapping, bad dtype or size), UNSUPPORTED
+ * (more than 2^31 - 1 runs, or runs of more than 64 Mi vectors), CUDA. */
+int wsfft_transpose_outer(const void *in, void *out, int64_t A, int64_t B, int64_t C,
+                          int dtype, wsfft_stream stream);
+
 /* Change the normalisation (a wsfft_norm).  Section 4.2.
  * Errors: INVALID_ARG. */
 int wsfft_plan_set_norm(wsfft_plan plan, int norm);

@@ -47,6 +47,7 @@ struct Plan {
     int64_t dims[3] = {1, 1, 1};
     int64_t batch = 1;
     int64_t elems = 1;  // per transform
+    int64_t axis_inner = 0;  // > 0: a plan of wsfft_plan_create_axis (one axis of length dims[0], stride axis_inner)
     int dtype = 0, dir = -1, norm = 0;
     std::vector<PassSpec> passes;
     std::map<int, std::pair<int, int>> overrides;  // pass index -> (E, tile)

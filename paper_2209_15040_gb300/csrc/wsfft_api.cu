@@ -528,7 +528,25 @@ int Plan::build_schedule() {
         eng_grid > 0) {
         return build_engine(d[0], d[1], inv);
     }
-    if (layout == WSFFT_LAYOUT_SWAPPED) {
+    if (axis_inner > 0) {
+        // wsfft_plan_create_axis: one superstep along an axis of length
+        // dims[0] whose consecutive elements are axis_inner apart; pencils
+        // (b, i) for batch index b and i < axis_inner
+        PassSpec p{};
+        p.N = (int)dims[0];
+        p.kind = axis_inner == 1 ? PASS_CONTIG : PASS_STRIDED;
+        p.E = default_E(p.N);
+        tune(p, axis_inner);
+        p.inner = axis_inner;
+        p.npencils_per_batch = axis_inner;
+        p.transform_elems = dims[0] * axis_inner;
+        p.src = SRC_IN;
+        p.dst = DST_OUT;
+        p.conj_in = inv;
+        p.conj_out = inv;
+        p.scale = axis_scale(dims[0], dir, norm);
+        passes.push_back(p);
+    } else if (layout == WSFFT_LAYOUT_SWAPPED) {
         // Spectral side with the last two axes swapped (the wafer's order,
         // Section 4.2).  The superstep along the last axis of the natural
         // side stores its pencils transposed (the four-step's staged store:
@@ -1070,6 +1088,44 @@ int wsfft_plan_create(wsfft_plan *plan, const int64_t *dims, int rank, int dtype
     return WSFFT_SUCCESS;
 }
 
+int wsfft_plan_create_axis(wsfft_plan *plan, int64_t n, int64_t inner, int dtype, int direction, int64_t batch) {
+    if (!plan) return WSFFT_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (batch < 1 || inner < 1) return WSFFT_ERR_INVALID_ARG;
+    if (dtype != WSFFT_C32 && dtype != WSFFT_C16F && dtype != WSFFT_C16BF) return WSFFT_ERR_INVALID_ARG;
+    if (direction != WSFFT_FORWARD && direction != WSFFT_INVERSE) return WSFFT_ERR_INVALID_ARG;
+    if (!is_pow2(n) || n > 4096 || !is_pow2(inner) || inner > ((int64_t)1 << 40)) return WSFFT_ERR_INVALID_SIZE;
+    Plan *p = new (std::nothrow) Plan();
+    if (!p) return WSFFT_ERR_ALLOC;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return WSFFT_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    p->eng_grid = p->sm_count;
+    p->rank = 1;
+    p->dims[0] = n;
+    p->axis_inner = inner;
+    p->dtype = dtype;
+    p->dir = direction;
+    p->batch = batch;
+    p->norm = dtype == WSFFT_C32 ? WSFFT_NORM_PAPER : WSFFT_NORM_ORTHO;
+    p->elems = n * inner;
+    if (cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) {
+        p->d_status = nullptr;
+        delete p;
+        return WSFFT_ERR_ALLOC;
+    }
+    int rc = p->zero(p->d_status, sizeof(int));
+    if (rc == WSFFT_SUCCESS) rc = p->build_schedule();
+    if (rc != WSFFT_SUCCESS) {
+        delete p;
+        return rc;
+    }
+    *plan = reinterpret_cast<wsfft_plan>(p);
+    return WSFFT_SUCCESS;
+}
+
 int wsfft_plan_set_norm(wsfft_plan plan, int norm) {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || norm < WSFFT_NORM_PAPER || norm > WSFFT_NORM_FORWARD) return WSFFT_ERR_INVALID_ARG;
@@ -1081,7 +1137,7 @@ int wsfft_plan_set_norm(wsfft_plan plan, int norm) {
 int wsfft_plan_set_layout(wsfft_plan plan, int layout) {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || (layout != WSFFT_LAYOUT_NATURAL && layout != WSFFT_LAYOUT_SWAPPED)) return WSFFT_ERR_INVALID_ARG;
-    if (p->ragged) return WSFFT_ERR_UNSUPPORTED;
+    if (p->ragged || (p->axis_inner > 0 && layout != WSFFT_LAYOUT_NATURAL)) return WSFFT_ERR_UNSUPPORTED;
     if (layout == WSFFT_LAYOUT_SWAPPED) {
         // the transposing store is built for pencils of 64..4096 points, and
         // its tiles need the row count to be a multiple of their pencils per

@@ -41,7 +41,7 @@ EXPORTS = (
     "wsfft_destroy", "wsfft_plan_create_ragged", "wsfft_execute_ragged", "wsfft_autotune",
     "wsfft_plan_sync_status", "wsfft_plan_passes", "wsfft_plan_profile",
     "wsfft_plan_set_pass_variant", "wsfft_plan_set_engine", "wsfft_plan_set_wait_test",
-    "wsfft_plan_launch_times", "wsfft_status_string",
+    "wsfft_plan_launch_times", "wsfft_status_string", "wsfft_plan_create_axis", "wsfft_transpose_outer",
 )
 
 
@@ -81,6 +81,8 @@ def lib():
         L.wsfft_plan_set_wait_test.argtypes = [P, ci, i64]
         L.wsfft_plan_launch_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), ci,
                                               ctypes.POINTER(ci)]
+        L.wsfft_plan_create_axis.argtypes = [ctypes.POINTER(P), i64, i64, ci, ci, i64]
+        L.wsfft_transpose_outer.argtypes = [P, P, i64, i64, i64, ci, P]
         L.wsfft_status_string.argtypes = [ci]
         L.wsfft_status_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -195,6 +197,31 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class AxisPlan(Plan):
+    """``batch`` x ``inner`` 1D transforms of length ``n`` along the middle
+    axis of a [batch][n][inner] array (see wsfft_plan_create_axis)."""
+
+    def __init__(self, n: int, inner: int, dtype: int = C32, direction: int = FORWARD, batch: int = 1,
+                 norm: int | None = None):
+        self.dims = (int(n),)
+        self.inner = int(inner)
+        self.dtype, self.direction, self.batch = int(dtype), int(direction), int(batch)
+        h = ctypes.c_void_p()
+        _check(lib().wsfft_plan_create_axis(ctypes.byref(h), int(n), self.inner, self.dtype, self.direction,
+                                            self.batch), "wsfft_plan_create_axis")
+        self._h = h
+        self.norm = NORM_PAPER if self.dtype == C32 else NORM_ORTHO
+        if norm is not None:
+            self.set_norm(norm)
+
+
+def transpose_outer(in_ptr: int, out_ptr: int, a: int, b: int, c: int, dtype: int = C32, stream=None) -> None:
+    """out[b][a][c] = in[a][b][c] on the device (see wsfft_transpose_outer)."""
+    _check(lib().wsfft_transpose_outer(ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(a), int(b), int(c),
+                                       int(dtype), ctypes.c_void_p(_stream_handle(stream))),
+           "wsfft_transpose_outer")
 
 
 class RaggedPlan:
