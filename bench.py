@@ -274,6 +274,24 @@ def sizes_leg(W, dev, stream, hbm_peak, steps=20, warmup=3):
     return out
 
 
+def layouts_leg(W, x, y, stream, us_natural, steps=20, warmup=3):
+    """The same 512^3 complex64 step (forward + inverse per transform pair)
+    with the spectral side in the other layouts: swapped (the last two axes
+    swapped) and the wafer's [n2][n0][n1]; three trips each, like natural
+    order."""
+    out = {"natural_us": round(us_natural, 2)}
+    for name, code in (("swapped", W.LAYOUT_SWAPPED), ("wafer", W.LAYOUT_WAFER)):
+        f = W.Plan(DIMS, W.C32, W.FORWARD, 1)
+        i = W.Plan(DIMS, W.C32, W.INVERSE, 1)
+        f.set_layout(code)
+        i.set_layout(code)
+        ms = timed_pairs(f, i, x, y, steps, warmup, 1, stream)
+        out[name + "_us"] = round(ms / steps * 1e3 / 2, 2)
+        f.close()
+        i.close()
+    return out
+
+
 def autograd_leg(W, dev, stream, steps=20, warmup=3):
     """The differentiable configuration: batch 8 x 128^3 complex64 (N(0,1)),
     loss = sum |W * FFT3(x)|^2 with W real uniform[0,1) of the same shape;
@@ -641,6 +659,10 @@ def main():
     if not args.no_sizes and world == 1:
         sizes = sizes_leg(W, dev, stream, hbm_peak)
 
+    layouts = None
+    if not args.no_sizes and world == 1:
+        layouts = layouts_leg(W, x, y, stream, us_per_transform)
+
     grad = None
     if not args.no_autograd and world == 1:
         grad = autograd_leg(W, dev, stream)
@@ -696,6 +718,8 @@ def main():
             line["ragged_batch"] = ragged
         if sizes:
             line["other_sizes"] = sizes
+        if layouts:
+            line["spectral_layouts"] = layouts
         if grad:
             line["autograd"] = grad
         if cpu:

@@ -95,7 +95,13 @@ typedef enum {
      * The middle axis ends contiguous, as on the wafer after its two
      * transposes (Section 4.2: each PE ends holding a pencil of that axis);
      * the two axes the wafer spreads over its mesh keep the input's order */
-    WSFFT_LAYOUT_SWAPPED = 1
+    WSFFT_LAYOUT_SWAPPED = 1,
+    /* rank 3 only: the wafer's own arrangement of the spectrum, [n2][n0][n1]
+     * -- X[k0][k1][k2] at k2*n0*n1 + k0*n1 + k1.  Section 4.2 transforms z,
+     * swaps x and z within mesh rows, transforms x, swaps x and y within
+     * mesh columns, transforms y; with the PEs numbered the way the input
+     * is (x outer), the spectrum ends on PE (k2, k0) holding the k1 pencil */
+    WSFFT_LAYOUT_WAFER = 2
 } wsfft_layout;
 
 typedef enum {
@@ -167,7 +173,11 @@ int wsfft_plan_set_norm(wsfft_plan plan, int norm);
  * (three trips for rank 3, two for rank 2) and never uses the fused
  * schedules of wsfft_plan_set_engine.  On this hardware the natural order
  * costs nothing extra; the swapped one serves callers that work on a
- * spectrum with the middle axis in memory.  Resets pass-shape choices
+ * spectrum with the middle axis in memory.  WSFFT_LAYOUT_WAFER needs rank
+ * 3 with every axis in [64, 4096]; its forward runs z with the transposing
+ * store (natural -> [n2][n0][n1], into the workspace), then y (now
+ * contiguous) and x; its inverse runs y and then x with the transposing
+ * store and z last -- again three trips.  Resets pass-shape choices
  * (wsfft_plan_set_pass_variant).
  * Errors: INVALID_ARG (bad enum), UNSUPPORTED (rank or sizes, ragged plan),
  * ALLOC. */

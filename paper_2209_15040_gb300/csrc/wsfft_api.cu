@@ -546,6 +546,96 @@ int Plan::build_schedule() {
         p.conj_out = inv;
         p.scale = axis_scale(dims[0], dir, norm);
         passes.push_back(p);
+    } else if (layout == WSFFT_LAYOUT_WAFER) {
+        // Spectral side in the wafer's own order [n2][n0][n1] (Section 4.2:
+        // after z is transformed, x and z swap places, then x and y; with the
+        // PEs numbered like the input, X[k0][k1][k2] ends at k2 * n0 * n1 +
+        // k0 * n1 + k1).  Built from the transposing store (pencil (t, row)
+        // element k to t*N*rows + k*rows + row), three trips as in natural
+        // order:
+        //   forward:  z with the transposed store, rows n0*n1 (in -> work):
+        //             [n0][n1][n2] -> [n2][n0][n1]; y contiguous (work ->
+        //             out); x strided with stride n1 (out, in place)
+        //   inverse:  y with the transposed store, rows n2*n0 (in -> work):
+        //             [n2][n0][n1] -> [n1][n2][n0]; x with the transposed
+        //             store, rows n1*n2 (work -> out): -> [n0][n1][n2]; z
+        //             contiguous (out, in place)
+        const int64_t n0 = dims[0], n1 = dims[1], n2 = dims[2];
+        const int64_t total = n0 * n1 * n2;
+        const int64_t per = total * elem_bytes(dtype);
+        chunk = std::max<int64_t>(1, std::min<int64_t>(batch, ((int64_t)4096 << 20) / per));
+        work_elems = chunk * total;
+        auto trans = [&](int64_t n, int64_t rows, int src, int dst) {
+            PassSpec t{};
+            t.kind = PASS_CONTIG;
+            t.N = (int)n;
+            t.E = default_E(t.N);
+            if (t.N == 1024 && dtype == WSFFT_C32) {
+                t.E = 32;  // as in the four-step: one warp per pencil, 8 per block
+                t.tile = 8;
+            }
+            t.variant = true;
+            t.inner = 1;
+            t.npencils_per_batch = rows;
+            t.trans_rows = rows;
+            t.src = src;
+            t.dst = dst;
+            t.scale = axis_scale(n, dir, norm);
+            t.transform_elems = total;
+            return t;
+        };
+        if (!inv) {
+            passes.push_back(trans(n2, n0 * n1, SRC_IN, DST_WORK));
+            PassSpec c{};
+            c.kind = PASS_CONTIG;
+            c.N = (int)n1;
+            c.E = default_E(c.N);
+            tune(c, 1);
+            c.inner = 1;
+            c.npencils_per_batch = n2 * n0;
+            c.src = SRC_WORK;
+            c.dst = DST_OUT;
+            c.scale = axis_scale(n1, dir, norm);
+            c.transform_elems = total;
+            passes.push_back(c);
+            PassSpec a{};
+            a.kind = PASS_STRIDED;
+            a.N = (int)n0;
+            a.E = default_E(a.N);
+            tune(a, n1);
+            a.inner = n1;
+            a.npencils_per_batch = n2 * n1;
+            a.src = SRC_OUT;
+            a.dst = DST_OUT;
+            a.scale = axis_scale(n0, dir, norm);
+            a.transform_elems = total;
+            passes.push_back(a);
+        } else {
+            passes.push_back(trans(n1, n2 * n0, SRC_IN, DST_WORK));
+            passes.push_back(trans(n0, n1 * n2, SRC_WORK, DST_OUT));
+            PassSpec c{};
+            c.kind = PASS_CONTIG;
+            c.N = (int)n2;
+            c.E = default_E(c.N);
+            tune(c, 1);
+            c.inner = 1;
+            c.npencils_per_batch = n0 * n1;
+            c.src = SRC_OUT;
+            c.dst = DST_OUT;
+            c.scale = axis_scale(n2, dir, norm);
+            c.transform_elems = total;
+            passes.push_back(c);
+        }
+        passes.front().conj_in = inv;
+        passes.back().conj_out = inv;
+        if (dtype == WSFFT_C32 && norm != WSFFT_NORM_ORTHO) {
+            double total_scale = 1.0;
+            for (auto &q : passes) {
+                total_scale *= q.scale;
+                q.scale = 1.f;
+            }
+            passes.back().scale = (float)total_scale;
+        }
     } else if (layout == WSFFT_LAYOUT_SWAPPED) {
         // Spectral side with the last two axes swapped (the wafer's order,
         // Section 4.2).  The superstep along the last axis of the natural
@@ -1136,8 +1226,17 @@ int wsfft_plan_set_norm(wsfft_plan plan, int norm) {
 
 int wsfft_plan_set_layout(wsfft_plan plan, int layout) {
     Plan *p = reinterpret_cast<Plan *>(plan);
-    if (!p || (layout != WSFFT_LAYOUT_NATURAL && layout != WSFFT_LAYOUT_SWAPPED)) return WSFFT_ERR_INVALID_ARG;
+    if (!p || (layout != WSFFT_LAYOUT_NATURAL && layout != WSFFT_LAYOUT_SWAPPED && layout != WSFFT_LAYOUT_WAFER))
+        return WSFFT_ERR_INVALID_ARG;
     if (p->ragged || (p->axis_inner > 0 && layout != WSFFT_LAYOUT_NATURAL)) return WSFFT_ERR_UNSUPPORTED;
+    if (layout == WSFFT_LAYOUT_WAFER) {
+        // every axis passes through the transposing store in one direction
+        // or the other: 64..4096 points each (its row counts, products of
+        // two axes, are then multiples of its pencils per block)
+        if (p->rank != 3) return WSFFT_ERR_UNSUPPORTED;
+        for (int i = 0; i < 3; ++i)
+            if (p->dims[i] < 64 || p->dims[i] > 4096) return WSFFT_ERR_UNSUPPORTED;
+    }
     if (layout == WSFFT_LAYOUT_SWAPPED) {
         // the transposing store is built for pencils of 64..4096 points, and
         // its tiles need the row count to be a multiple of their pencils per

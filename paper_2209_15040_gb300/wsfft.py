@@ -20,7 +20,7 @@ import torch
 C32, C16F, C16BF = 0, 1, 2
 FORWARD, INVERSE = -1, 1
 NORM_PAPER, NORM_NONE, NORM_ORTHO, NORM_FORWARD = 0, 1, 2, 3
-LAYOUT_NATURAL, LAYOUT_SWAPPED = 0, 1
+LAYOUT_NATURAL, LAYOUT_SWAPPED, LAYOUT_WAFER = 0, 1, 2
 NORMS = {"paper": NORM_PAPER, "none": NORM_NONE, "ortho": NORM_ORTHO, "forward": NORM_FORWARD}
 
 SUCCESS = 0
@@ -156,7 +156,8 @@ class Plan:
         return n.value, b.value
 
     def set_layout(self, layout: int) -> None:
-        """Spectral-side layout: LAYOUT_NATURAL or LAYOUT_SWAPPED (last two axes swapped)."""
+        """Spectral-side layout: LAYOUT_NATURAL, LAYOUT_SWAPPED (last two axes
+        swapped) or LAYOUT_WAFER (rank 3: [n2][n0][n1], the wafer's order)."""
         _check(lib().wsfft_plan_set_layout(self._h, int(layout)), "wsfft_plan_set_layout")
 
     def set_pass_variant(self, pass_index: int, values_per_thread: int, tile: int) -> None:

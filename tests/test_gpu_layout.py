@@ -1,7 +1,8 @@
-"""GPU parity of the swapped spectral layout (the middle axis in memory, as
-on the wafer after its two transposes, Section 4.2): the forward writes its
-result with the last two axes swapped, the inverse reads its input that way;
-the spatial side is natural.  Compared with the FP64 oracle's natural result with those two
+"""GPU parity of the spectral layouts other than natural order: the swapped
+layout (the middle axis in memory, as on the wafer after its two
+transposes, Section 4.2: the last two axes swapped) and, for rank 3, the
+wafer's own arrangement [n2][n0][n1].  The forward writes its result in the
+layout, the inverse reads its input in it; the spatial side is natural.  Compared with the FP64 oracle's natural result with those two
 axes swapped, for every storage type, rank 2 and 3, batches, in place and
 out of place, and sizes that reach the tuned 512-point kernel shapes."""
 import numpy as np
@@ -172,3 +173,95 @@ def test_swapped_layout_autotune_cache(tmp_path, monkeypatch):
     torch.cuda.synchronize()
     plan2.close()
     assert oracle.rel_l2(to_host_c128(y, "c32"), ref) < TOL["c32"]
+
+
+# -- the wafer's own rank-3 arrangement [n2][n0][n1] ----------------------------
+
+def _run_wafer(x, dims, dtype, direction, batch, inplace):
+    plan = W.Plan(dims, DT[dtype], direction, batch, _norm(dtype))
+    plan.set_layout(W.LAYOUT_WAFER)
+    assert plan.passes()[0] == 3
+    out = x.clone() if inplace else torch.empty_like(x)
+    plan.execute(out.data_ptr() if inplace else x.data_ptr(), out.data_ptr())
+    torch.cuda.synchronize()
+    assert plan.sync_status() == W.SUCCESS
+    plan.close()
+    return out
+
+
+def _to_wafer(a):
+    """[..., n0, n1, n2] -> [..., n2, n0, n1]"""
+    return np.moveaxis(a, -1, -3)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape", [(2, 64, 128, 256), (1, 256, 64, 128), (1, 128, 512, 64)])
+@pytest.mark.parametrize("inplace", [False, True])
+def test_forward_wafer(dtype, shape, inplace):
+    xs, xc = seeded(shape, 15, "uniform", dtype)
+    x = to_device(xs, dtype)
+    out = _run_wafer(x, shape[1:], dtype, W.FORWARD, shape[0], inplace)
+    n0, n1, n2 = shape[1:]
+    y = to_host_c128(out, dtype).reshape((shape[0], n2, n0, n1))
+    ref = _to_wafer(oracle.fftn(xc, rank=3, norm=_norm(dtype)))
+    err = oracle.rel_l2(y, ref)
+    print(f"{shape} {dtype} forward wafer in_place={inplace}: rel_l2={err:.3e}")
+    assert err < TOL[dtype], err
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape", [(2, 64, 128, 256), (1, 128, 512, 64)])
+@pytest.mark.parametrize("inplace", [False, True])
+def test_inverse_from_wafer(dtype, shape, inplace):
+    # the device buffer holds a spectrum X[k0][k1][k2] stored as [k2][k0][k1]
+    n0, n1, n2 = shape[1:]
+    wshape = (shape[0], n2, n0, n1)
+    xs, xc = seeded(wshape, 16, "uniform", dtype)
+    x = to_device(xs, dtype)
+    out = _run_wafer(x, shape[1:], dtype, W.INVERSE, shape[0], inplace)
+    y = to_host_c128(out, dtype).reshape(shape)
+    spec = np.moveaxis(xc, -3, -1)  # back to [k0][k1][k2]
+    ref = oracle.fftn(spec, rank=3, sign=+1, norm=_norm(dtype))
+    err = oracle.rel_l2(y, ref)
+    print(f"{shape} {dtype} inverse from wafer in_place={inplace}: rel_l2={err:.3e}")
+    assert err < TOL[dtype], err
+
+
+def test_wafer_512_cube_forward_and_round_trip():
+    # the bench workload's size: every spectral element against the oracle,
+    # then the inverse from the wafer layout back to the input
+    n = 512
+    xs, xc = seeded((n, n, n), 17, "normal", "c32")
+    x = to_device(xs, "c32")
+    f = W.Plan((n, n, n), W.C32, W.FORWARD, 1)
+    i = W.Plan((n, n, n), W.C32, W.INVERSE, 1)
+    f.set_layout(W.LAYOUT_WAFER)
+    i.set_layout(W.LAYOUT_WAFER)
+    y = torch.empty_like(x)
+    f.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.complex128)
+    ref = _to_wafer(oracle.fftn(xc))
+    err = oracle.rel_l2(got, ref)
+    del got, ref
+    print(f"512^3 wafer forward rel_l2 {err:.3e}")
+    assert err < TOL["c32"]
+    i.execute(y.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    assert f.sync_status() == W.SUCCESS and i.sync_status() == W.SUCCESS
+    rt = (torch.linalg.vector_norm(y - x) / torch.linalg.vector_norm(x)).item()
+    assert rt < 5e-6, rt
+    f.close()
+    i.close()
+
+
+def test_wafer_layout_rejections():
+    p2 = W.Plan((64, 64), W.C32, W.FORWARD, 1)
+    with pytest.raises(RuntimeError):
+        p2.set_layout(W.LAYOUT_WAFER)  # rank 2 (its wafer order is LAYOUT_SWAPPED)
+    p2.close()
+    p3 = W.Plan((64, 32, 64), W.C32, W.FORWARD, 1)
+    with pytest.raises(RuntimeError):
+        p3.set_layout(W.LAYOUT_WAFER)  # an axis below 64
+    p3.set_layout(W.LAYOUT_NATURAL)
+    p3.close()
