@@ -346,22 +346,9 @@ def autograd_leg(W, dev, stream, steps=20, warmup=3):
             "note": "step includes torch's elementwise loss and its gradient; the 128 MiB batch sits in L2"}
 
 
-def ragged_leg(W, dev, stream, reps=5):
-    """The ragged configuration (256 uneven 3D shapes from seed 4, N(0,1)):
-    one persistent launch replayed from a captured CUDA graph vs one plan
-    execute per instance (3 launches each)."""
-    from paper_2209_15040_gb300 import inputs
-    shapes = inputs.ragged_shapes(256, 4)
-    g = torch.Generator(device=dev)
-    xs, ys = [], []
-    for i, s in enumerate(shapes):
-        g.manual_seed(1000 + i)
-        xs.append(torch.view_as_complex(torch.randn(tuple(int(v) for v in s) + (2,), generator=g,
-                                                    device=dev)).contiguous())
-        ys.append(torch.empty_like(xs[-1]))
-    elems = int(sum(int(np.prod(s)) for s in shapes))
-    ins, outs = [x.data_ptr() for x in xs], [y.data_ptr() for y in ys]
-    plan = W.RaggedPlan(shapes, W.C32, W.FORWARD)
+def _ragged_graph_time(plan, ins, outs, dev, stream, reps):
+    """Microseconds per replay of the ragged plan's launch captured in a
+    CUDA graph (CUDA events on the stream, after warm-up replays)."""
     side = torch.cuda.Stream(dev)
     with torch.cuda.stream(side):
         plan.execute(ins, outs, side)
@@ -378,7 +365,45 @@ def ragged_leg(W, dev, stream, reps=5):
         graph.replay()
     e1.record(stream)
     torch.cuda.synchronize()
-    t_graph = e0.elapsed_time(e1) / reps * 1e3
+    return e0.elapsed_time(e1) / reps * 1e3
+
+
+def ragged_leg(W, dev, stream, reps=5):
+    """The ragged configuration (256 uneven 3D shapes from seed 4, N(0,1)):
+    one persistent launch replayed from a captured CUDA graph, with the
+    default tile shapes and after wsfft_autotune, vs one plan execute per
+    instance (3 launches each)."""
+    from paper_2209_15040_gb300 import inputs
+    shapes = inputs.ragged_shapes(256, 4)
+    g = torch.Generator(device=dev)
+    xs, ys = [], []
+    for i, s in enumerate(shapes):
+        g.manual_seed(1000 + i)
+        xs.append(torch.view_as_complex(torch.randn(tuple(int(v) for v in s) + (2,), generator=g,
+                                                    device=dev)).contiguous())
+        ys.append(torch.empty_like(xs[-1]))
+    elems = int(sum(int(np.prod(s)) for s in shapes))
+    ins, outs = [x.data_ptr() for x in xs], [y.data_ptr() for y in ys]
+    plan = W.RaggedPlan(shapes, W.C32, W.FORWARD)
+    # the default tile shapes and lag, then the autotuned choice (tile shape
+    # per axis length, queue lag), each replayed from a captured graph
+    t_default = _ragged_graph_time(plan, ins, outs, dev, stream, reps)
+    import tempfile
+    tune = {}
+    with tempfile.TemporaryDirectory() as td:
+        prev = os.environ.get("WSFFT_TUNE_CACHE")
+        os.environ["WSFFT_TUNE_CACHE"] = os.path.join(td, "tune.jsonl")
+        try:
+            plan.autotune()
+            with open(os.environ["WSFFT_TUNE_CACHE"]) as fh:
+                rec = json.loads(fh.read().strip().splitlines()[-1])
+            tune = {"shape_select": rec["variants"][0][1], "lag": rec["mode"]}
+        finally:
+            if prev is None:
+                del os.environ["WSFFT_TUNE_CACHE"]
+            else:
+                os.environ["WSFFT_TUNE_CACHE"] = prev
+    t_graph = _ragged_graph_time(plan, ins, outs, dev, stream, reps)
     plans = [W.Plan(tuple(int(v) for v in s), W.C32, W.FORWARD, 1) for s in shapes]
     launches = sum(p.passes()[0] for p in plans)
     def per_instance():
@@ -387,6 +412,7 @@ def ragged_leg(W, dev, stream, reps=5):
     for _ in range(2):
         per_instance()
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
         per_instance()
@@ -397,7 +423,8 @@ def ragged_leg(W, dev, stream, reps=5):
         p.close()
     plan.close()
     return {"instances": len(shapes), "elements": elems, "bytes": elems * 8,
-            "persistent_graph_us": round(t_graph, 1), "per_instance_us": round(t_inst, 1),
+            "persistent_graph_us": round(t_graph, 1), "persistent_graph_default_us": round(t_default, 1),
+            "autotuned": tune, "per_instance_us": round(t_inst, 1),
             "speedup": round(t_inst / t_graph, 3), "launches_persistent": 1,
             "launches_per_instance": launches,
             "hbm_gbs_3pass_equiv": round(3 * 2 * elems * 8 / (t_graph * 1e-6) / 1e9, 1)}

@@ -235,9 +235,24 @@ int wsfft_execute_ragged(wsfft_plan plan, const void *const *in, void *const *ou
 /* Time the kernel variants that apply to this plan on `stream` (with
  * temporary buffers) and keep the fastest; results are cached in the JSON
  * file named by WSFFT_TUNE_CACHE (if set), keyed by device name, SM count,
- * shape, batch, dtype, direction, normalisation and spectral layout.
+ * shape, batch, dtype, direction, normalisation and spectral layout.  For a
+ * ragged plan the candidates are the tile shape of each axis length that
+ * occurs and the queue lag (wsfft_plan_set_ragged_variant), the key holds
+ * the sorted multiset of instance shapes, and a ragged plan created later
+ * with the same key takes the cached choice.
  * Errors: ALLOC, CUDA. */
 int wsfft_autotune(wsfft_plan plan, wsfft_stream stream);
+
+/* Ragged plans: choose the tile shape per axis length and the queue lag.
+ * Bit k of shape_select (k = log2(N) - 5, N in 32..256) selects the second
+ * tile shape for axes of length N (values per thread: 16 instead of 8 for
+ * N <= 64, 8 instead of 16 for N >= 128; a tile is always 256 threads);
+ * `lag` L puts the y tiles of instance s - L and the x tiles of instance
+ * s - 2L after the z tiles of instance s in the queue (1 = the default).
+ * Waits for the plan's own work, then rebuilds its tile queue.  Used by
+ * wsfft_autotune.  Errors: INVALID_ARG (shape_select outside 0..15, lag
+ * outside 1..64), UNSUPPORTED (not a ragged plan), ALLOC, CUDA. */
+int wsfft_plan_set_ragged_variant(wsfft_plan plan, int shape_select, int lag);
 
 /* Choose the kernel shape of pass `pass` (0-based, in launch order) of this
  * plan: `values_per_thread` complex values per thread (the radix of the

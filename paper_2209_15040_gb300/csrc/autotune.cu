@@ -10,12 +10,19 @@
 // on temporary buffers of the plan's size: two warm-up executes, then the
 // mean of three, timed with CUDA events on the caller's stream.
 //
+// Ragged plans: the tile shape of each axis length that occurs (two per
+// length, kernel ragged.cuh) greedily, then the queue lag between an
+// instance's supersteps (1, 2 or 4), on temporary buffers, timed the same
+// way.
+//
 // Cache: when WSFFT_TUNE_CACHE names a file, each result is appended as one
 // JSON object per line, keyed by device name, SM count, shape, batch, storage
-// type, direction and normalisation; a later autotune (or plan creation) for
-// the same key reads the choice back instead of timing.
+// type, direction and normalisation (ragged plans: the sorted multiset of
+// instance shapes instead of shape and batch); a later autotune (or plan
+// creation) for the same key reads the choice back instead of timing.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <array>
 #include <cstdio>
 #include <cstdlib>
@@ -145,12 +152,143 @@ std::vector<std::pair<int, int>> shapes_for(int kind, int N, int dtype) {
     return {};
 }
 
+// -- ragged plans: the tile shape per axis length and the queue lag -------------
+
+// Key of a ragged plan: device, storage type, direction, normalisation and
+// the multiset of instance shapes (sorted, so the order of the instances
+// does not matter), hashed (FNV-1a 64) with the count beside it.
+std::string ragged_key(const Plan &p) {
+    cudaDeviceProp prop;
+    std::string name = "unknown";
+    if (cudaGetDeviceProperties(&prop, p.device) == cudaSuccess) name = prop.name;
+    std::vector<std::array<int64_t, 3>> shapes((size_t)p.rag_count);
+    for (int i = 0; i < p.rag_count; ++i)
+        for (int d = 0; d < 3; ++d) shapes[i][d] = p.rag_dims[3 * (size_t)i + d];
+    std::sort(shapes.begin(), shapes.end());
+    uint64_t h = 1469598103934665603ull;
+    for (auto &sh : shapes)
+        for (int d = 0; d < 3; ++d) {
+            h ^= (uint64_t)sh[d];
+            h *= 1099511628211ull;
+        }
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s|sm%d|ragged%d|%016llx|t%d|d%d|n%d", name.c_str(), p.sm_count, p.rag_count,
+             (unsigned long long)h, p.dtype, p.dir, p.norm);
+    return buf;
+}
+
+// the ragged choice is stored in the same line format: mode = lag,
+// variants = [[-1, shape selection, 0]]
+int apply_ragged(Plan &p, const Choice &c) {
+    int sel = 0;
+    for (auto &v : c.variants)
+        if (v[0] == -1) sel = v[1];
+    if (sel < 0 || sel > 15 || c.mode < 1 || c.mode > 64) return WSFFT_ERR_INVALID_ARG;
+    p.rag_esel = sel;
+    p.rag_lag = c.mode;
+    return p.rag_build();
+}
+
+double time_ragged(Plan &p, const std::vector<const void *> &in, const std::vector<void *> &out, cudaStream_t st) {
+    auto run = [&]() {
+        return wsfft_execute_ragged(reinterpret_cast<wsfft_plan>(&p), in.data(), out.data(), (wsfft_stream)st) ==
+               WSFFT_SUCCESS;
+    };
+    if (!run()) return -1.0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return -1.0;
+    }
+    cudaEventRecord(e0, st);
+    bool ok = true;
+    for (int i = 0; i < 3 && ok; ++i) ok = run();
+    cudaEventRecord(e1, st);
+    float ms = -1.f;
+    if (ok && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) return -1.0;
+    return ok && ms >= 0.f ? ms * 1e3 / 3.0 : -1.0;
+}
+
+int autotune_ragged(Plan &p, cudaStream_t st) {
+    const std::string key = ragged_key(p);
+    Choice cached;
+    if (load(key, cached)) return apply_ragged(p, cached);
+    const size_t eb = p.dtype == WSFFT_C32 ? 8 : 4;
+    const size_t bytes = (size_t)p.elems * eb;
+    char *in = nullptr, *out = nullptr;
+    if (cudaMalloc(&in, bytes) != cudaSuccess) return WSFFT_ERR_ALLOC;
+    if (cudaMalloc(&out, bytes) != cudaSuccess) {
+        cudaFree(in);
+        return WSFFT_ERR_ALLOC;
+    }
+    cudaMemsetAsync(in, 0, bytes, st);
+    std::vector<const void *> ip((size_t)p.rag_count);
+    std::vector<void *> op((size_t)p.rag_count);
+    int present = 0;  // bit log2(N) - 5 for every axis length that occurs
+    size_t off = 0;
+    for (int i = 0; i < p.rag_count; ++i) {
+        int64_t e = 1;
+        for (int d = 0; d < 3; ++d) {
+            const int64_t n = p.rag_dims[3 * (size_t)i + d];
+            e *= n;
+            int lg = 0;
+            while ((int64_t)1 << lg < n) ++lg;
+            present |= 1 << (lg - 5);
+        }
+        ip[i] = in + off;
+        op[i] = out + off;
+        off += (size_t)e * eb;  // a multiple of 16 bytes (axes >= 32)
+    }
+    const int saved_sel = p.rag_esel, saved_lag = p.rag_lag;
+    Choice best;
+    best.mode = saved_lag;
+    best.variants = {{-1, saved_sel, 0}};
+    double best_us = 1e300;
+    auto consider = [&](int sel, int lag) {
+        Choice c;
+        c.mode = lag;
+        c.variants = {{-1, sel, 0}};
+        if (apply_ragged(p, c) != WSFFT_SUCCESS) return;
+        const double us = time_ragged(p, ip, op, st);
+        if (us > 0 && us < best_us) {
+            best_us = us;
+            best = c;
+        }
+    };
+    consider(0, 1);
+    for (int k = 0; k < 4; ++k)  // greedy: each present length's other shape
+        if (present & (1 << k)) consider(best.variants[0][1] ^ (1 << k), best.mode);
+    const int sel = best.variants[0][1];
+    for (int lag : {2, 4}) consider(sel, lag);
+    cudaStreamSynchronize(st);
+    cudaFree(in);
+    cudaFree(out);
+    cudaGetLastError();
+    if (best_us >= 1e300) {
+        p.rag_esel = saved_sel;
+        p.rag_lag = saved_lag;
+        p.rag_build();
+        return WSFFT_ERR_CUDA;
+    }
+    const int rc = apply_ragged(p, best);
+    if (rc == WSFFT_SUCCESS) save(key, best, best_us);
+    return rc;
+}
+
 }  // namespace
 
 // Apply a cached choice at plan creation (no timing).  Returns true if one
 // was applied.
 bool autotune_apply_cached(Plan &p) {
     Choice c;
+    if (p.ragged) {
+        if (!load(ragged_key(p), c)) return false;
+        return apply_ragged(p, c) == WSFFT_SUCCESS;
+    }
     if (!load(plan_key(p), c)) return false;
     return apply(p, c) == WSFFT_SUCCESS;
 }
@@ -162,7 +300,7 @@ using namespace wsfft;
 extern "C" int wsfft_autotune(wsfft_plan plan, wsfft_stream stream) {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p) return WSFFT_ERR_INVALID_ARG;
-    if (p->ragged) return WSFFT_SUCCESS;  // one schedule: nothing to choose
+    if (p->ragged) return autotune_ragged(*p, (cudaStream_t)stream);
     const std::string key = plan_key(*p);
     Choice cached;
     if (load(key, cached)) return apply(*p, cached);

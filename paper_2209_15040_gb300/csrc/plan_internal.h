@@ -83,7 +83,11 @@ struct Plan {
     void *rag_inst_host = nullptr;  // pinned host copy (pointers filled per execute)
     cudaEvent_t rag_copied = nullptr;
     bool rag_uploaded = false;
-    const float2 *rag_tw[9] = {};
+    const float2 *rag_tw[4][2] = {};  // stage tables per length 32..256 and tile shape
+    std::vector<int64_t> rag_dims;     // count x 3 axis lengths
+    int rag_esel = 0;                  // bit log2(N) - 5: length N uses its second tile shape
+    int rag_lag = 1;                   // queue distance (instances) between an instance's supersteps
+    int64_t rag_items_cap = 0;
     bool withhold = false;         // testing: drop one completion signal
     std::vector<cudaEvent_t> prof_ev;  // 2 per launch slot when profiling
     int prof_used = 0;                 // launch slots recorded since the last read
@@ -96,6 +100,7 @@ struct Plan {
     int build_schedule();
     int build_engine(int64_t n0, int64_t n, bool inv);
     int build_slab(int64_t n0, int64_t n, bool inv);
+    int rag_build();                   // ragged plans: instance records and tile queue
     bool slab_runs(int n);             // cluster-fused pass A resident on this device
     int slab_checked[2] = {0, 0};      // per slab edge 256 / 512: 0 unknown, 1 yes, -1 no
     int run(const void *in, void *out, cudaStream_t st);

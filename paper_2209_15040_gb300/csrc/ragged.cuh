@@ -8,11 +8,13 @@
 //   z tiles (contiguous axis, P whole pencils), signal the instance's z counter
 //   y tiles (middle axis, W adjacent pencils), wait for all z tiles, signal y
 //   x tiles (outer axis, W adjacent pencils), wait for all y tiles.
-// The queue interleaves instances (z of instance s, y of s-1, x of s-2), so
-// an instance is usually still in L2 when its next superstep reads it, and
-// a tile only ever waits for tiles with smaller tickets (deadlock-free with
-// any number of resident blocks).  Axis lengths 32..256 are dispatched at run
-// time inside the kernel; every tile kind uses the same 256 threads.
+// The queue interleaves instances (z of instance s, y of s-L, x of s-2L for
+// a lag L the plan chooses, 1 by default), so an instance is usually still in
+// L2 when its next superstep reads it, and a tile only ever waits for tiles
+// with smaller tickets (deadlock-free with any number of resident blocks).
+// Axis lengths 32..256 and their tile shape (one of two per length, chosen
+// by the plan) are dispatched at run time inside the kernel; every tile kind
+// uses the same 256 threads.
 #pragma once
 
 #include "engine.cuh"
@@ -43,7 +45,8 @@ struct RagArgs {
     const RagInst *inst;
     uint32_t *ctr;         // [0] tickets, [1 + 2*i] z done of instance i, [2 + 2*i] y done
     int *status;
-    const float2 *tw[9];   // stage tables indexed by log2(N) - 1 .. (N = 2..512), per N
+    const float2 *tw[4][2];  // stage tables [log2(N) - 5][shape] for N = 32..256
+    int esel;              // bit log2(N) - 5 set: axes of length N use their second shape
     float ci;              // +1, or -1: conjugate on the z load (inverse)
     float co;              // +1, or -1: conjugate on the x store (inverse)
     uint64_t timeout_ns;
@@ -51,40 +54,43 @@ struct RagArgs {
 
 constexpr int RAG_THREADS = 256;
 
-__host__ __device__ constexpr int rag_E(int N) { return N <= 64 ? 8 : 16; }
-__host__ __device__ constexpr int rag_T(int N) { return N / rag_E(N); }
-__host__ __device__ constexpr int rag_P(int N) { return RAG_THREADS / rag_T(N); }  // z pencils per tile
-__host__ __device__ constexpr int rag_W(int N) { return RAG_THREADS / rag_T(N); }  // y/x pencils per tile
-__host__ __device__ constexpr int rag_smem_elems() {
-    // max over N in {32..256} of the contiguous and strided exchange buffers
-    return 4608;
+// Two tile shapes per axis length N (values per thread E; a tile is 256
+// threads, T = N/E per pencil, 256/T pencils): shape 0 is the default, shape
+// 1 the alternative the autotuner may pick per length.
+__host__ __device__ constexpr int rag_E(int N, int alt = 0) {
+    return alt ? (N <= 64 ? 16 : 8) : (N <= 64 ? 8 : 16);
 }
-static_assert(rag_P(32) * contig_PS(32) <= 4608 && rag_P(64) * contig_PS(64) <= 4608 &&
-                  rag_P(128) * contig_PS(128) <= 4608 && rag_P(256) * contig_PS(256) <= 4608,
-              "contiguous exchange fits");
-static_assert(32 * rag_W(32) * 17 / 16 <= 4608 && 64 * rag_W(64) * 17 / 16 <= 4608 &&
-                  128 * rag_W(128) * 17 / 16 <= 4608 && 256 * rag_W(256) * 17 / 16 <= 4608,
-              "strided exchange fits");
+__host__ __device__ constexpr int rag_T(int N, int alt = 0) { return N / rag_E(N, alt); }
+__host__ __device__ constexpr int rag_P(int N, int alt = 0) { return RAG_THREADS / rag_T(N, alt); }  // z pencils per tile
+__host__ __device__ constexpr int rag_W(int N, int alt = 0) { return RAG_THREADS / rag_T(N, alt); }  // y/x pencils per tile
+constexpr int RAG_SMEM = 5120;  // float2: the largest exchange buffer of any shape below
+__host__ __device__ constexpr int rag_smem_elems() { return RAG_SMEM; }
+__host__ __device__ constexpr bool rag_fits(int N, int alt) {
+    return rag_P(N, alt) * contig_PS(N) <= RAG_SMEM && N * rag_W(N, alt) * 17 / 16 <= RAG_SMEM;
+}
+static_assert(rag_fits(32, 0) && rag_fits(64, 0) && rag_fits(128, 0) && rag_fits(256, 0) && rag_fits(32, 1) &&
+                  rag_fits(64, 1) && rag_fits(128, 1) && rag_fits(256, 1),
+              "exchange buffers fit");
 
-template <int N, class S>
+template <int N, int ALT, class S>
 __device__ __forceinline__ void rag_contig(const RagInst &I, int tile, const float2 *tw, float ci,
                                            float sc, float2 *smem) {
-    constexpr int T = rag_T(N), P = rag_P(N);
+    constexpr int T = rag_T(N, ALT), P = rag_P(N, ALT);
     const int t = threadIdx.x % T, p = threadIdx.x / T;
     const int64_t npen = (int64_t)I.n[0] * I.n[1];
     const int64_t q = (int64_t)tile * P + p;
     ContigAcc<S, OP_DEF, OP_DEF, false, (T <= 32)> acc{reinterpret_cast<const S *>(I.in) + q * N,
                                      reinterpret_cast<S *>(I.out) + q * N, smem + p * contig_PS(N), ci,
                                      {sc, sc}, q < npen};
-    pencil_fft<N, rag_E(N)>(acc, t, tw);
+    pencil_fft<N, rag_E(N, ALT)>(acc, t, tw);
 }
 
 // strided superstep along axis d (1: y, inner n2; 2: x, inner n1*n2), read
 // and written in `out` (L2-coherent loads: other blocks wrote it this launch)
-template <int N, class S>
+template <int N, int ALT, class S>
 __device__ __forceinline__ void rag_strided(const RagInst &I, int d, int tile, const float2 *tw,
                                             float sx, float sy, float2 *smem) {
-    constexpr int T = rag_T(N), W = rag_W(N);
+    constexpr int T = rag_T(N, ALT), W = rag_W(N, ALT);
     const int w = threadIdx.x % W, t = threadIdx.x / W;
     const int log_inner = d == 1 ? I.log_n2 : I.log_n12;
     const int64_t inner = (int64_t)1 << log_inner;
@@ -107,30 +113,33 @@ __device__ __forceinline__ void rag_strided(const RagInst &I, int d, int tile, c
     acc.tw_shift = 0;
     acc.tw_mask = 0;
     (void)T;
-    pencil_fft<N, rag_E(N)>(acc, t, tw);
+    pencil_fft<N, rag_E(N, ALT)>(acc, t, tw);
+}
+
+template <int N, class S>
+__device__ __forceinline__ void rag_tile_n(const RagArgs &a, const RagInst &I, int d, int tile, float2 *smem,
+                                           const float2 *tw0, const float2 *tw1, int alt) {
+    if (d == 0) {
+        if (alt) rag_contig<N, 1, S>(I, tile, tw1, a.ci, I.scale[0], smem);
+        else rag_contig<N, 0, S>(I, tile, tw0, a.ci, I.scale[0], smem);
+    } else {
+        const float sx = I.scale[d], sy = d == 2 ? a.co * I.scale[d] : I.scale[d];
+        if (alt) rag_strided<N, 1, S>(I, d, tile, tw1, sx, sy, smem);
+        else rag_strided<N, 0, S>(I, d, tile, tw0, sx, sy, smem);
+    }
 }
 
 template <class S>
 __device__ __forceinline__ void rag_tile(const RagArgs &a, const RagInst &I, int d, int tile,
                                          float2 *smem) {
     const int N = I.n[2 - d];
-    // stage tables by log2(N) - 1, with constant indices (a run-time index
-    // into the parameter array would copy it to local memory)
-    if (d == 0) {
-        switch (N) {
-            case 32: rag_contig<32, S>(I, tile, a.tw[4], a.ci, I.scale[0], smem); break;
-            case 64: rag_contig<64, S>(I, tile, a.tw[5], a.ci, I.scale[0], smem); break;
-            case 128: rag_contig<128, S>(I, tile, a.tw[6], a.ci, I.scale[0], smem); break;
-            default: rag_contig<256, S>(I, tile, a.tw[7], a.ci, I.scale[0], smem); break;
-        }
-    } else {
-        const float sx = I.scale[d], sy = d == 2 ? a.co * I.scale[d] : I.scale[d];
-        switch (N) {
-            case 32: rag_strided<32, S>(I, d, tile, a.tw[4], sx, sy, smem); break;
-            case 64: rag_strided<64, S>(I, d, tile, a.tw[5], sx, sy, smem); break;
-            case 128: rag_strided<128, S>(I, d, tile, a.tw[6], sx, sy, smem); break;
-            default: rag_strided<256, S>(I, d, tile, a.tw[7], sx, sy, smem); break;
-        }
+    // stage tables with constant indices (a run-time index into the
+    // parameter array would copy it to local memory)
+    switch (N) {
+        case 32: rag_tile_n<32, S>(a, I, d, tile, smem, a.tw[0][0], a.tw[0][1], a.esel & 1); break;
+        case 64: rag_tile_n<64, S>(a, I, d, tile, smem, a.tw[1][0], a.tw[1][1], a.esel & 2); break;
+        case 128: rag_tile_n<128, S>(a, I, d, tile, smem, a.tw[2][0], a.tw[2][1], a.esel & 4); break;
+        default: rag_tile_n<256, S>(a, I, d, tile, smem, a.tw[3][0], a.tw[3][1], a.esel & 8); break;
     }
 }
 

@@ -1042,6 +1042,84 @@ int Plan::run_host_pipelined(const void *hin, void *hout, cudaStream_t st) {
     return WSFFT_SUCCESS;
 }
 
+// (Re)build a ragged plan's instance records and tile queue for its current
+// tile-shape selection and lag: tile counts per superstep follow the chosen
+// shape of each axis length; the queue holds z tiles of instance s, y tiles
+// of s - lag and x tiles of s - 2*lag, so every wait is on smaller tickets.
+int Plan::rag_build() {
+    const int count = rag_count;
+    if (wait_own_work() != WSFFT_SUCCESS) return WSFFT_ERR_CUDA;  // no execute may still read the tables
+    if (rag_uploaded && cudaEventSynchronize(rag_copied) != cudaSuccess) return WSFFT_ERR_CUDA;
+    for (int k = 0; k < 4; ++k)
+        for (int alt = 0; alt < 2; ++alt) {
+            rag_tw[k][alt] = table(32 << k, rag_E(32 << k, alt));
+            if (!rag_tw[k][alt]) return WSFFT_ERR_ALLOC;
+        }
+    auto alt_of = [&](int64_t N) { return (rag_esel >> (ilog2(N) - 5)) & 1; };
+    std::vector<RagInst> inst((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        RagInst &I = inst[i];
+        memset(&I, 0, sizeof(I));
+        for (int d = 0; d < 3; ++d) I.n[d] = (int)rag_dims[3 * (size_t)i + d];
+        I.log_n2 = ilog2(I.n[2]);
+        I.log_n12 = ilog2((int64_t)I.n[1] * I.n[2]);
+        const int64_t n0 = I.n[0], n1 = I.n[1], n2 = I.n[2];
+        const int64_t P = rag_P((int)n2, alt_of(n2)), W1 = rag_W((int)n1, alt_of(n1)), W0 = rag_W((int)n0, alt_of(n0));
+        I.tiles[0] = (int)((n0 * n1 + P - 1) / P);
+        I.tiles[1] = (int)((n0 * n2 + W1 - 1) / W1);
+        I.tiles[2] = (int)((n1 * n2 + W0 - 1) / W0);
+        // scales of the z, y, x supersteps
+        I.scale[0] = axis_scale(n2, dir, norm);
+        I.scale[1] = axis_scale(n1, dir, norm);
+        I.scale[2] = axis_scale(n0, dir, norm);
+    }
+    const int L = rag_lag;
+    std::vector<RagItem> items;
+    for (int s = 0; s < count + 2 * L; ++s) {
+        if (s < count)
+            for (int t = 0; t < inst[s].tiles[0]; ++t) items.push_back(RagItem{ITEM_SIGNAL | (0 << 8), s, t, 0});
+        if (s - L >= 0 && s - L < count)
+            for (int t = 0; t < inst[s - L].tiles[1]; ++t)
+                items.push_back(RagItem{ITEM_STRIDED | ITEM_WAIT | ITEM_SIGNAL | (1 << 8), s - L, t, 0});
+        if (s - 2 * L >= 0 && s - 2 * L < count)
+            for (int t = 0; t < inst[s - 2 * L].tiles[2]; ++t)
+                items.push_back(RagItem{ITEM_STRIDED | ITEM_WAIT | (2 << 8), s - 2 * L, t, 0});
+    }
+    if (items.size() > (size_t)0x7fffffff) return WSFFT_ERR_UNSUPPORTED;
+    const size_t ib = items.size() * sizeof(RagItem), nb = inst.size() * sizeof(RagInst);
+    if (items.size() > (size_t)rag_items_cap) {
+        if (rag_items) cudaFree(rag_items);
+        rag_items = nullptr;
+        rag_items_cap = 0;
+        if (cudaMalloc(&rag_items, ib) != cudaSuccess) {
+            rag_items = nullptr;
+            return WSFFT_ERR_ALLOC;
+        }
+        rag_items_cap = (int64_t)items.size();
+    }
+    if (!rag_inst) {
+        if (cudaMalloc(&rag_inst, nb) != cudaSuccess) {
+            rag_inst = nullptr;
+            return WSFFT_ERR_ALLOC;
+        }
+        if (cudaMallocHost(&rag_inst_host, nb) != cudaSuccess) {
+            rag_inst_host = nullptr;
+            return WSFFT_ERR_ALLOC;
+        }
+    } else {
+        // keep the pointers of the last execute; the tile counts changed
+        const RagInst *old = static_cast<const RagInst *>(rag_inst_host);
+        for (int i = 0; i < count; ++i) {
+            inst[i].in = old[i].in;
+            inst[i].out = old[i].out;
+        }
+    }
+    memcpy(rag_inst_host, inst.data(), nb);
+    rag_uploaded = false;  // the next execute uploads the records again
+    rag_nitems = (int)items.size();
+    return upload(rag_items, items.data(), ib);
+}
+
 int Plan::upload(void *dst, const void *src, size_t bytes) {
     if (!setup_st && cudaStreamCreateWithFlags(&setup_st, cudaStreamNonBlocking) != cudaSuccess) {
         setup_st = nullptr;
@@ -1450,59 +1528,13 @@ int wsfft_plan_create_ragged(wsfft_plan *plan, int count, const int64_t *dims, i
         return fail(WSFFT_ERR_ALLOC);
     }
     if (p->zero(p->d_status, sizeof(int)) != WSFFT_SUCCESS) return fail(WSFFT_ERR_CUDA);
-    std::vector<RagInst> inst((size_t)count);
-    for (int i = 0; i < count; ++i) {
-        RagInst &I = inst[i];
-        memset(&I, 0, sizeof(I));
-        for (int d = 0; d < 3; ++d) I.n[d] = (int)dims[3 * i + d];
-        I.log_n2 = ilog2(I.n[2]);
-        I.log_n12 = ilog2((int64_t)I.n[1] * I.n[2]);
-        const int64_t n0 = I.n[0], n1 = I.n[1], n2 = I.n[2];
-        I.tiles[0] = (int)((n0 * n1 + rag_P((int)n2) - 1) / rag_P((int)n2));
-        I.tiles[1] = (int)((n0 * n2 + rag_W((int)n1) - 1) / rag_W((int)n1));
-        I.tiles[2] = (int)((n1 * n2 + rag_W((int)n0) - 1) / rag_W((int)n0));
-        // scales of the z, y, x supersteps
-        I.scale[0] = axis_scale(n2, direction, p->norm);
-        I.scale[1] = axis_scale(n1, direction, p->norm);
-        I.scale[2] = axis_scale(n0, direction, p->norm);
-        for (int d = 0; d < 3; ++d) {
-            const int N = I.n[d];
-            const float2 *t = p->table(N, rag_E(N));
-            if (!t) return fail(WSFFT_ERR_ALLOC);
-            p->rag_tw[ilog2(N) - 1] = t;
-        }
-    }
+    p->rag_dims.assign(dims, dims + 3 * (size_t)count);
     p->elems = 0;
-    for (auto &I : inst) p->elems += (int64_t)I.n[0] * I.n[1] * I.n[2];
-    // queue: z tiles of instance s, y tiles of s-1, x tiles of s-2
-    std::vector<RagItem> items;
-    for (int s = 0; s < count + 2; ++s) {
-        if (s < count)
-            for (int t = 0; t < inst[s].tiles[0]; ++t) items.push_back(RagItem{ITEM_SIGNAL | (0 << 8), s, t, 0});
-        if (s - 1 >= 0 && s - 1 < count)
-            for (int t = 0; t < inst[s - 1].tiles[1]; ++t)
-                items.push_back(RagItem{ITEM_STRIDED | ITEM_WAIT | ITEM_SIGNAL | (1 << 8), s - 1, t, 0});
-        if (s - 2 >= 0)
-            for (int t = 0; t < inst[s - 2].tiles[2]; ++t)
-                items.push_back(RagItem{ITEM_STRIDED | ITEM_WAIT | (2 << 8), s - 2, t, 0});
+    for (int i = 0; i < count; ++i) p->elems += dims[3 * i] * dims[3 * i + 1] * dims[3 * i + 2];
+    {
+        const int rc = p->rag_build();
+        if (rc != WSFFT_SUCCESS) return fail(rc);
     }
-    if (items.size() > (size_t)0x7fffffff) return fail(WSFFT_ERR_UNSUPPORTED);
-    p->rag_nitems = (int)items.size();
-    const size_t ib = items.size() * sizeof(RagItem), nb = inst.size() * sizeof(RagInst);
-    if (cudaMalloc(&p->rag_items, ib) != cudaSuccess) {
-        p->rag_items = nullptr;
-        return fail(WSFFT_ERR_ALLOC);
-    }
-    if (cudaMalloc(&p->rag_inst, nb) != cudaSuccess) {
-        p->rag_inst = nullptr;
-        return fail(WSFFT_ERR_ALLOC);
-    }
-    if (cudaMallocHost(&p->rag_inst_host, nb) != cudaSuccess) {
-        p->rag_inst_host = nullptr;
-        return fail(WSFFT_ERR_ALLOC);
-    }
-    memcpy(p->rag_inst_host, inst.data(), nb);
-    if (p->upload(p->rag_items, items.data(), ib) != WSFFT_SUCCESS) return fail(WSFFT_ERR_CUDA);
     if (cudaMalloc(&p->d_ctr, (size_t)(1 + 2 * count) * sizeof(uint32_t)) != cudaSuccess) {
         p->d_ctr = nullptr;
         return fail(WSFFT_ERR_ALLOC);
@@ -1519,8 +1551,25 @@ int wsfft_plan_create_ragged(wsfft_plan *plan, int count, const int64_t *dims, i
                                           : launch_ragged_c16bf(dummy, &per_sm, 0, 0);
     if (e != cudaSuccess || per_sm < 1) return fail(WSFFT_ERR_CUDA);
     p->rag_grid = per_sm * p->sm_count;
+    autotune_apply_cached(*p);  // a remembered tile-shape choice and lag for this shape set, if any
     *plan = reinterpret_cast<wsfft_plan>(p);
     return WSFFT_SUCCESS;
+}
+
+int wsfft_plan_set_ragged_variant(wsfft_plan plan, int shape_select, int lag) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || shape_select < 0 || shape_select > 15 || lag < 1 || lag > 64) return WSFFT_ERR_INVALID_ARG;
+    if (!p->ragged) return WSFFT_ERR_UNSUPPORTED;
+    const int old_sel = p->rag_esel, old_lag = p->rag_lag;
+    p->rag_esel = shape_select;
+    p->rag_lag = lag;
+    const int rc = p->rag_build();
+    if (rc != WSFFT_SUCCESS) {
+        p->rag_esel = old_sel;
+        p->rag_lag = old_lag;
+        p->rag_build();
+    }
+    return rc;
 }
 
 int wsfft_execute_ragged(wsfft_plan plan, const void *const *in, void *const *out,
@@ -1555,7 +1604,9 @@ int wsfft_execute_ragged(wsfft_plan plan, const void *const *in, void *const *ou
     a.inst = static_cast<const RagInst *>(p->rag_inst);
     a.ctr = p->d_ctr;
     a.status = p->d_status;
-    for (int i = 0; i < 9; ++i) a.tw[i] = p->rag_tw[i];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 2; ++j) a.tw[i][j] = p->rag_tw[i][j];
+    a.esel = p->rag_esel;
     a.ci = p->dir == WSFFT_INVERSE ? -1.f : 1.f;
     a.co = a.ci;
     a.timeout_ns = (uint64_t)p->wait_timeout_ns;

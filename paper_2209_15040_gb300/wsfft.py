@@ -42,6 +42,7 @@ EXPORTS = (
     "wsfft_plan_sync_status", "wsfft_plan_passes", "wsfft_plan_profile",
     "wsfft_plan_set_pass_variant", "wsfft_plan_set_engine", "wsfft_plan_set_wait_test",
     "wsfft_plan_launch_times", "wsfft_status_string", "wsfft_plan_create_axis", "wsfft_transpose_outer",
+    "wsfft_plan_set_ragged_variant",
 )
 
 
@@ -83,6 +84,7 @@ def lib():
                                               ctypes.POINTER(ci)]
         L.wsfft_plan_create_axis.argtypes = [ctypes.POINTER(P), i64, i64, ci, ci, i64]
         L.wsfft_transpose_outer.argtypes = [P, P, i64, i64, i64, ci, P]
+        L.wsfft_plan_set_ragged_variant.argtypes = [P, ci, ci]
         L.wsfft_status_string.argtypes = [ci]
         L.wsfft_status_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -250,6 +252,15 @@ class RaggedPlan:
 
     def sync_status(self, stream=None) -> int:
         return int(lib().wsfft_plan_sync_status(self._h, ctypes.c_void_p(_stream_handle(stream))))
+
+    def set_variant(self, shape_select: int, lag: int = 1) -> None:
+        """Tile shape per axis length (bit log2(N) - 5) and queue lag (see
+        wsfft_plan_set_ragged_variant)."""
+        _check(lib().wsfft_plan_set_ragged_variant(self._h, int(shape_select), int(lag)),
+               "wsfft_plan_set_ragged_variant")
+
+    def autotune(self, stream=None) -> None:
+        _check(lib().wsfft_autotune(self._h, ctypes.c_void_p(_stream_handle(stream))), "wsfft_autotune")
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -33,7 +33,7 @@ def test_autotune_cube_and_cache(tmp_path, monkeypatch):
     lines = cache.read_text().strip().splitlines()
     assert len(lines) == 1
     entry = json.loads(lines[0])
-    assert entry["mode"] in (0, 1, 2, 3) and entry["us"] > 0
+    assert entry["mode"] in (0, 1, 2, 3, 4) and entry["us"] > 0
     plan.execute(x.data_ptr(), y.data_ptr())
     torch.cuda.synchronize()
     ref = oracle.fftn(xs.astype(np.complex128))
@@ -91,3 +91,39 @@ def test_autotune_half_storage_512(monkeypatch, dtype, code):
     tol = 3e-3 if dtype == "c16f" else 2e-2
     assert oracle.rel_l2(got, ref) < tol
     plan.close()
+
+
+def test_autotune_ragged_caches_a_choice(tmp_path, monkeypatch):
+    # the ragged plan's tile shapes per axis length and its queue lag are
+    # timed, the choice is cached under the shape multiset, the tuned plan
+    # matches the oracle, and a plan created later for the same shapes (in
+    # another order) finds the cached entry instead of timing again
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("WSFFT_TUNE_CACHE", str(cache))
+    shapes = inputs.ragged_shapes(24, 4)
+    xs = [inputs.complex_input(tuple(int(v) for v in s), 700 + i, "normal", "c32") for i, s in enumerate(shapes)]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    outs = [torch.empty_like(x) for x in xd]
+    plan = W.RaggedPlan(shapes, W.C32, W.FORWARD)
+    plan.autotune()
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 1
+    entry = json.loads(lines[0])
+    assert "ragged24" in entry["key"] and entry["us"] > 0
+    assert 1 <= entry["mode"] <= 4 and entry["variants"][0][0] == -1 and 0 <= entry["variants"][0][1] <= 15
+    plan.execute([x.data_ptr() for x in xd], [y.data_ptr() for y in outs])
+    torch.cuda.synchronize()
+    assert plan.sync_status() == W.SUCCESS
+    plan.close()
+    for x, y in zip(xs, outs):
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.fftn(x.astype(np.complex128))) < 5e-6
+    plan2 = W.RaggedPlan(shapes[::-1], W.C32, W.FORWARD)
+    plan2.autotune()
+    assert len(cache.read_text().strip().splitlines()) == 1
+    for y in outs:
+        y.zero_()
+    plan2.execute([x.data_ptr() for x in xd[::-1]], [y.data_ptr() for y in outs[::-1]])
+    torch.cuda.synchronize()
+    plan2.close()
+    for x, y in zip(xs, outs):
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.fftn(x.astype(np.complex128))) < 5e-6

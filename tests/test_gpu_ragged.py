@@ -124,3 +124,51 @@ def test_ragged_under_cuda_graph():
             assert oracle.rel_l2(y.cpu().numpy(), oracle.fftn(x.astype(np.complex128))) < TOL["c32"]
     assert plan.sync_status() == W.SUCCESS
     plan.close()
+
+
+def _run_variant(shapes, xs, xd, dtype, direction, sel, lag):
+    outs = [torch.empty_like(x) for x in xd]
+    plan = W.RaggedPlan(shapes, DT[dtype], direction)
+    plan.set_variant(sel, lag)
+    plan.execute([x.data_ptr() for x in xd], [y.data_ptr() for y in outs])
+    torch.cuda.synchronize()
+    assert plan.sync_status() == W.SUCCESS
+    plan.close()
+    norm = oracle.NORM_PAPER if dtype == "c32" else oracle.NORM_ORTHO
+    worst = 0.0
+    for x, y in zip(xs, outs):
+        ref = oracle.fftn(inputs.storage_to_c128(x, dtype), sign=direction, norm=norm)
+        worst = max(worst, oracle.rel_l2(to_host_c128(y, dtype), ref))
+    return worst
+
+
+def test_ragged_every_tile_shape_selection():
+    # all 16 selections of the second tile shape per axis length, on shapes
+    # that use every length 32..256 on every axis
+    shapes = np.array([[32, 64, 128], [256, 32, 64], [128, 256, 32], [64, 128, 256], [32, 32, 256],
+                       [256, 64, 32]])
+    xs, xd = make_inputs(shapes, "c32", 500)
+    for sel in range(16):
+        err = _run_variant(shapes, xs, xd, "c32", W.FORWARD if sel % 2 else W.INVERSE, sel, 1)
+        assert err < TOL["c32"], (sel, err)
+
+
+@pytest.mark.parametrize("dtype,sel,lag", [("c32", 15, 2), ("c32", 5, 4), ("c32", 0, 7), ("c16f", 15, 3),
+                                           ("c16bf", 10, 2)])
+def test_ragged_queue_lag(dtype, sel, lag):
+    shapes = inputs.ragged_shapes(20, 9)
+    xs, xd = make_inputs(shapes, dtype, 600)
+    err = _run_variant(shapes, xs, xd, dtype, W.FORWARD, sel, lag)
+    assert err < TOL[dtype], err
+
+
+def test_ragged_variant_rejections():
+    plan = W.RaggedPlan(np.array([[32, 32, 32]]), W.C32, W.FORWARD)
+    with pytest.raises(RuntimeError):
+        plan.set_variant(16, 1)
+    with pytest.raises(RuntimeError):
+        plan.set_variant(0, 0)
+    plan.close()
+    p = W.Plan((32, 32, 32), W.C32, W.FORWARD, 1)
+    assert W.lib().wsfft_plan_set_ragged_variant(p.handle, 0, 1) == W.ERR_UNSUPPORTED
+    p.close()
