@@ -115,7 +115,7 @@ def allmax(world, v: float) -> float:
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons while running."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
@@ -139,7 +139,32 @@ class Clocks:
         except Exception:
             self.proc = None
 
-    def stop(self):
+    @staticmethod
+    def parse(lines, window=None):
+        """Median SM clock, max clock and throttle reasons of the samples
+        whose timestamp lies in `window` (host seconds since the epoch,
+        start and end), or of all samples when none does."""
+        from datetime import datetime
+        rows = []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                ts = datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]),
+                             [nm for nm, v in zip(names, parts[4:8]) if v.lower() == "active"]))
+            except ValueError:
+                continue
+        inside = [r for r in rows if window and window[0] - 0.01 <= r[0] <= window[1] + 0.01]
+        use = inside or rows
+        reasons = sorted({nm for r in use for nm in r[3]})
+        return {"sm_mhz": statistics.median(r[1] for r in use) if use else None,
+                "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "reasons": reasons, "samples": len(use), "samples_in_timed_region": len(inside)}
+
+    def stop(self, window=None):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -148,28 +173,13 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 7:
-                    continue
-                try:
-                    sm.append(float(parts[0]))
-                    smax.append(float(parts[1]))
-                except ValueError:
-                    continue
-                for nm, v in zip(names, parts[3:7]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
+            out = self.parse(f.readlines(), window)
         try:
             os.remove(self.path)
         except OSError:
             pass
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return out
 
 
 def oracle_pair(x):
@@ -576,13 +586,17 @@ def main():
     launches_per_step = 2 * npass
 
     # --- timed region: FP32 pairs, per-launch events on the launching stream
+    # clock samples: the sampler starts before the warm-up (nvidia-smi takes a
+    # while to start) and only the samples stamped inside the timed region count
     clocks = Clocks(local)
+    clocks.start()
     timed_pairs(fwd, inv, x, y, 0, args.warmup, world, stream)  # warm-up, not recorded
     fwd.profile(args.steps * npass)
     inv.profile(args.steps * npass)
-    clocks.start()
+    t_region = [time.time(), 0.0]
     ms = timed_pairs(fwd, inv, x, y, args.steps, 0, world, stream)
-    clk = clocks.stop()
+    t_region[1] = time.time()
+    clk = clocks.stop(t_region)
     per_launch = fwd.launch_times(args.steps * npass) + inv.launch_times(args.steps * npass)
     fwd.profile(0)
     inv.profile(0)
@@ -653,7 +667,7 @@ def main():
         for _ in range(2):
             fwd.execute_host(hx.data_ptr(), hy.data_ptr(), stream)
             inv.execute_host(hy.data_ptr(), hy.data_ptr(), stream)
-        esteps = max(2, min(args.steps, 5))
+        esteps = max(2, min(args.steps, 10))
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()

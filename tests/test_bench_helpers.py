@@ -65,3 +65,19 @@ def test_device_info_is_safe_without_a_gpu():
     import torch
     info = bench.device_info(torch.device("cuda", 0))
     assert info is None or (isinstance(info["name"], str) and info["sms"] > 0)
+
+
+def test_clock_samples_filtered_to_the_timed_region():
+    from datetime import datetime
+    import bench
+
+    def line(ts, mhz, reason="Not Active"):
+        stamp = datetime.fromtimestamp(ts).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{stamp}, {mhz}, 2070, 500.0, {reason}, Not Active, Not Active, Not Active"
+
+    t0 = 1_800_000_000.0
+    lines = [line(t0 - 1.0, 900, "Active"), line(t0 + 0.02, 2070), line(t0 + 0.03, 2060), line(t0 + 2.0, 1000)]
+    out = bench.Clocks.parse(lines, (t0, t0 + 0.04))
+    assert out["samples_in_timed_region"] == 2 and out["sm_mhz"] == 2065 and out["reasons"] == []
+    out = bench.Clocks.parse(lines, (t0 + 5, t0 + 6))  # nothing inside: every sample counts
+    assert out["samples_in_timed_region"] == 0 and out["samples"] == 4 and out["reasons"] == ["hw_slowdown"]
