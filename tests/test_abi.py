@@ -95,3 +95,36 @@ def test_product_path_has_no_oracle_dependency():
                 src = open(os.path.join(dirpath, fn), errors="ignore").read()
                 assert "import oracle" not in src and "from oracle" not in src, fn
                 assert "fft_oracle" not in src, fn
+
+
+def test_new_entry_points_validate_on_the_host(lib):
+    # rejected before any CUDA call: runs without a GPU
+    h = ctypes.c_void_p()
+    assert lib.wsfft_plan_create_axis(None, 512, 16, W.C32, W.FORWARD, 1) == W.ERR_INVALID_ARG
+    assert lib.wsfft_plan_create_axis(ctypes.byref(h), 512, 16, W.C32, W.FORWARD, 0) == W.ERR_INVALID_ARG
+    assert lib.wsfft_plan_create_axis(ctypes.byref(h), 512, 16, 9, W.FORWARD, 1) == W.ERR_INVALID_ARG
+    assert lib.wsfft_plan_create_axis(ctypes.byref(h), 512, 16, W.C32, 0, 1) == W.ERR_INVALID_ARG
+    assert lib.wsfft_plan_create_axis(ctypes.byref(h), 500, 16, W.C32, W.FORWARD, 1) == W.ERR_INVALID_SIZE
+    assert lib.wsfft_plan_create_axis(ctypes.byref(h), 8192, 16, W.C32, W.FORWARD, 1) == W.ERR_INVALID_SIZE
+    assert lib.wsfft_plan_create_axis(ctypes.byref(h), 512, 24, W.C32, W.FORWARD, 1) == W.ERR_INVALID_SIZE
+    buf = (ctypes.c_char * 4096)()
+    p = ctypes.addressof(buf)
+    assert lib.wsfft_transpose_outer(None, p, 2, 2, 2, W.C32, None) == W.ERR_INVALID_ARG
+    assert lib.wsfft_transpose_outer(p, p, 2, 2, 2, W.C32, None) == W.ERR_INVALID_ARG          # in == out
+    assert lib.wsfft_transpose_outer(p, p + 32, 2, 2, 2, W.C32, None) == W.ERR_INVALID_ARG     # overlapping
+    assert lib.wsfft_transpose_outer(p, p + 2048, 0, 2, 2, W.C32, None) == W.ERR_INVALID_ARG   # empty axis
+    assert lib.wsfft_transpose_outer(p, p + 2048, 2, 2, 2, 5, None) == W.ERR_INVALID_ARG       # bad dtype
+    assert lib.wsfft_plan_set_ragged_variant(None, 0, 1) == W.ERR_INVALID_ARG
+    assert lib.wsfft_plan_set_engine(None, 4) == W.ERR_INVALID_ARG
+
+
+def test_distributed_rejects_bad_layouts():
+    from paper_2209_15040_gb300.distributed import SlabFFT3
+
+    class Dummy:
+        pass
+
+    with pytest.raises(ValueError):
+        SlabFFT3((64, 64), world=1, rank=0, local_forward=Dummy(), local_inverse=Dummy())
+    with pytest.raises(ValueError):
+        SlabFFT3((6, 8, 8), world=4, rank=0, local_forward=Dummy(), local_inverse=Dummy())
