@@ -145,7 +145,7 @@ std::vector<std::pair<int, int>> shapes_for(int kind, int N, int dtype) {
                 {8, PAIR_TILE + 32}, {8, PAIR_TILE + 8}, {16, PAIR_TILE + 16}, {16, PAIR_TILE + 32},
                 {16, SPLIT_TILE + 16}, {16, SPLIT_TILE + 32}, {8, SPLIT_TILE + 16}, {8, SPLIT_TILE + 32}};
     if (kind == PASS_STRIDED && N == 256) return {{16, 32}, {8, 16}, {8, PAIR_TILE + 16}};
-    if (kind == PASS_STRIDED && N == 1024) return {{16, 8}};
+    if (kind == PASS_STRIDED && N == 1024) return {{16, 8}, {32, 8}, {16, SPLIT_TILE + 8}};
     if (kind == PASS_CONTIG && N == 512)
         return {{32, 16}, {32, 8}, {32, 32}, {16, 8}, {8, 8}, {16, SPLIT_TILE + 8}, {16, SPLIT_TILE + 16}};
     if (kind == PASS_CONTIG && N == 256) return {{8, 8}};

@@ -167,6 +167,8 @@ cudaError_t launch_extra(int kind, int N, int E, int tile, const void *in, void 
         return cudaErrorInvalidValue;
     }
     if (kind == PASS_STRIDED && tile >= SPLIT_TILE) {
+        if (N == 1024 && E == 16 && tile == SPLIT_TILE + 8)
+            return launch_strided_pair<1024, 16, 8, S, true>(in, out, a, st);
         if (N == 512 && E == 16 && tile == SPLIT_TILE + 16)
             return launch_strided_pair<512, 16, 16, S, true>(in, out, a, st);
         if (N == 512 && E == 16 && tile == SPLIT_TILE + 32)

@@ -492,13 +492,21 @@ int Plan::build_schedule() {
             // measured at 1024^3: 32 values per thread (radix 32 x 32, one
             // exchange); contiguous: one warp per pencil, 8 per block;
             // strided: 16 pencils per block at strides of 2^17 elements
-            // and more (128-byte rows), 8 below (16-bit storage there
-            // with 16 values per thread)
+            // and more (128-byte rows: narrower tiles lost 10-50% there),
+            // below that split-form pencil pairs with 16 values per pencil
+            // and 8 pencils per block (two blocks per SM: 0.404 vs 0.427 ms
+            // for 32 values per thread on a 1 GiB array at stride 1024)
             p.E = 32;
             p.tile = 8;
             if (p.kind == PASS_STRIDED) {
-                if (inner >= ((int64_t)1 << 17)) p.tile = 16;
-                else if (dtype != WSFFT_C32) p.E = 16;
+                if (inner >= ((int64_t)1 << 17)) {
+                    p.tile = 16;
+                } else if (inner % 8 == 0) {
+                    p.E = 16;
+                    p.tile = SPLIT_TILE + 8;
+                } else if (dtype != WSFFT_C32) {
+                    p.E = 16;
+                }
             }
         }
         if (p.kind == PASS_STRIDED && p.N == 512 && inner % 16 == 0) {

@@ -141,6 +141,18 @@ def test_256_shapes(dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
+def test_1024_split_pairs(dtype):
+    # split-form pencil pairs at 1024 points, 8 pencils per block: the default
+    # strided shape below strides of 2^17 elements, selected explicitly and
+    # reached by default plans (inner 64, 256, 1024), both directions
+    run_variant((1024, 4, 16), 3, dtype, [(2, 16, SPLIT + 8)])
+    run_variant((2, 1024, 64), 3, dtype, [(1, 16, SPLIT + 8)], direction=W.INVERSE)
+    for shape, rank in (((2, 1024, 64), 3), ((1024, 256), 2), ((64, 1024, 1024), 3)):
+        run_variant(shape, rank, dtype, [])
+        run_variant(shape, rank, dtype, [], direction=W.INVERSE)
+
+
+@pytest.mark.parametrize("dtype", ["c32", "c16f", "c16bf"])
 def test_1024_shapes(dtype):
     for sh in CONTIG[1024]:
         run_variant((4, 8, 1024), 3, dtype, [(0, *sh)])
