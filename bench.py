@@ -198,16 +198,70 @@ def oracle_input(n=N_AXIS):
 
 def cpu_sample_oracle(reps: int = 3):
     """FP64 CPU oracle at the benchmark size: `reps` forward+inverse pairs of
-    the 512^3 transform (about 1-2 s each on 16 cores), median per transform."""
+    the 512^3 transform (about 1-2 s each on 16 cores), median per transform.
+    Also returns the oracle's input and its forward transform, for the
+    element-by-element check of the GPU path at the same size."""
     import oracle
     cores = len(os.sched_getaffinity(0))
     oracle.set_threads(cores)
     x = oracle_input()
-    times = [oracle_pair(x) for _ in range(reps)]
+    times, y_ref = [], None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        y = oracle.fftn(x, sign=-1)
+        oracle.fftn(y, sign=+1)
+        times.append(time.perf_counter() - t0)
+        if y_ref is None:
+            y_ref = y
     us = statistics.median(times) / 2 * 1e6
-    return {"value": round(us, 1), "unit": "us per 512^3 transform", "cores": oracle.get_threads(),
-            "kind": "oracle",
-            "sample": f"median of {reps} FP64 forward+inverse pairs at 512^3 (the benchmark size), /2"}
+    rec = {"value": round(us, 1), "unit": "us per 512^3 transform", "cores": oracle.get_threads(),
+           "kind": "oracle",
+           "sample": f"median of {reps} FP64 forward+inverse pairs at 512^3 (the benchmark size), /2"}
+    return rec, x, y_ref
+
+
+def parity_512(W, x_c128, y_ref, dev, stream):
+    """The GPU forward transform of the oracle's own 512^3 input, element by
+    element against the FP64 oracle's forward: complex64 (paper
+    normalisation), and FP16 / BF16 storage against the oracle run on the
+    16-bit-rounded input with the orthonormal scaling."""
+    import oracle
+    from paper_2209_15040_gb300 import inputs
+
+    def errs(got, ref):
+        d = got - ref
+        num = float(np.sqrt(np.sum(d.real ** 2 + d.imag ** 2)))
+        den = float(np.sqrt(np.sum(ref.real ** 2 + ref.imag ** 2)))
+        mabs = float(np.max(np.abs(d)))
+        return {"rel_l2": num / den, "max_abs": mabs, "max_abs_rel": mabs / float(np.max(np.abs(ref)))}
+
+    out = {}
+    xd = torch.from_numpy(x_c128.astype(np.complex64)).to(dev)
+    yd = torch.empty_like(xd)
+    p = W.Plan(DIMS, W.C32, W.FORWARD, 1)
+    p.execute(xd.data_ptr(), yd.data_ptr(), stream)
+    torch.cuda.synchronize()
+    p.close()
+    out["c32"] = errs(yd.cpu().numpy().astype(np.complex128), y_ref)
+    del xd, yd
+    for name, code, tdt in (("c16f", W.C16F, torch.float16), ("c16bf", W.C16BF, torch.bfloat16)):
+        xs = inputs.to_storage(np.stack([x_c128.real, x_c128.imag], axis=-1), name)
+        ref = oracle.fftn(inputs.storage_to_c128(xs, name), norm=oracle.NORM_ORTHO)
+        if name == "c16f":
+            xh = torch.from_numpy(np.ascontiguousarray(xs)).to(dev)
+        else:
+            xh = torch.from_numpy(np.ascontiguousarray(xs).view(np.int16)).view(torch.bfloat16).to(dev)
+        yh = torch.empty_like(xh)
+        p = W.Plan(DIMS, code, W.FORWARD, 1)
+        p.execute(xh.data_ptr(), yh.data_ptr(), stream)
+        torch.cuda.synchronize()
+        p.close()
+        got = yh.cpu()
+        got = got.numpy() if name == "c16f" else got.view(torch.int16).numpy().view(np.uint16)
+        out[name] = errs(inputs.storage_to_c128(got, name), ref)
+        del xh, yh, ref
+    out["note"] = "forward at 512^3 on the oracle's seeded N(0,1) input, every element against the FP64 oracle"
+    return out
 
 
 def run_reference(args, world, rank):
@@ -713,8 +767,11 @@ def main():
         ragged = ragged_leg(W, dev, stream)
 
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_sample_oracle()
+        cpu, x_or, y_or = cpu_sample_oracle()
+        parity = parity_512(W, x_or, y_or, dev, stream)
+        del x_or, y_or
 
     if rank == 0:
         line = {
@@ -765,6 +822,8 @@ def main():
             line["autograd"] = grad
         if cpu:
             line["cpu_baseline"] = cpu
+        if parity:
+            line["parity_vs_fp64_oracle"] = parity
         print(json.dumps(line), flush=True)
     for p in (fwd, inv):
         p.close()
