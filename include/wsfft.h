@@ -156,7 +156,7 @@ int wsfft_plan_create_axis(wsfft_plan *plan, int64_t n, int64_t inner, int dtype
  * asynchronous on `stream`.  Moves 16-byte vectors when C's byte length and
  * both pointers are multiples of 16.
  * Errors: INVALID_ARG (null, overlapping, bad dtype or size), UNSUPPORTED
- * (more than 2^31 - 1 runs, or runs of more than 64 Mi vectors), CUDA. */
+ * (more than 2^31 - 1 runs of c elements), CUDA. */
 int wsfft_transpose_outer(const void *in, void *out, int64_t A, int64_t B, int64_t C,
                           int dtype, wsfft_stream stream);
 

@@ -21,7 +21,8 @@ namespace wsfft {
 namespace {
 
 // V: vector type moved per access; c counted in vectors.  Block (x, y)
-// copies chunk y (up to 1024 vectors) of run x = a*B + b; its 256 threads
+// copies chunk y (up to 1024 vectors; then y + gridDim.y, ...) of run
+// x = a*B + b; its 256 threads
 // take consecutive vectors, four each, so every warp access is a contiguous
 // 512-byte run of both arrays (16-byte vectors) and four loads are in flight
 // per thread.
@@ -32,22 +33,28 @@ __global__ void __launch_bounds__(256) transpose_outer_kernel(const V *__restric
                                                               int64_t A, int B, int64_t Cv) {
     const int64_t run = blockIdx.x;
     const int64_t a = run / B, b = run - a * B;
-    const int64_t c0 = (int64_t)blockIdx.y * kChunk + threadIdx.x;
     const V *src = in + run * Cv;
     V *dst = out + (b * A + a) * Cv;
-    V v[kChunk / 256];
+    // chunks of one run: blockIdx.y, then every gridDim.y-th (runs of more
+    // than 65535 chunks)
+    for (int64_t ch = blockIdx.y; ch * kChunk < Cv; ch += gridDim.y) {
+        const int64_t c0 = ch * kChunk + threadIdx.x;
+        V v[kChunk / 256];
 #pragma unroll
-    for (int k = 0; k < kChunk / 256; ++k)
-        if (c0 + k * 256 < Cv) v[k] = src[c0 + k * 256];
+        for (int k = 0; k < kChunk / 256; ++k)
+            if (c0 + k * 256 < Cv) v[k] = src[c0 + k * 256];
 #pragma unroll
-    for (int k = 0; k < kChunk / 256; ++k)
-        if (c0 + k * 256 < Cv) dst[c0 + k * 256] = v[k];
+        for (int k = 0; k < kChunk / 256; ++k)
+            if (c0 + k * 256 < Cv) dst[c0 + k * 256] = v[k];
+    }
 }
 
 template <class V>
 cudaError_t launch_transpose(const void *in, void *out, int64_t A, int64_t B, int64_t Cv, cudaStream_t st) {
-    const int64_t runs = A * B, chunks = (Cv + kChunk - 1) / kChunk;
-    if (runs > 0x7fffffffLL || chunks > 65535 || B > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const int64_t runs = A * B;
+    int64_t chunks = (Cv + kChunk - 1) / kChunk;
+    if (chunks > 65535) chunks = 65535;
+    if (runs > 0x7fffffffLL || B > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     transpose_outer_kernel<V><<<dim3((unsigned)runs, (unsigned)chunks), 256, 0, st>>>(
         static_cast<const V *>(in), static_cast<V *>(out), A, (int)B, Cv);
     return cudaGetLastError();

@@ -52,7 +52,8 @@ def test_axis_plan(dtype, n, inner, batch, direction):
 
 
 @pytest.mark.parametrize("dtype", ["c32", "c16f"])
-@pytest.mark.parametrize("a,b,c", [(4, 2, 65536), (2, 4, 512), (3, 5, 7), (1, 8, 1), (16, 16, 3), (64, 8, 1024)])
+@pytest.mark.parametrize("a,b,c", [(4, 2, 65536), (2, 4, 512), (3, 5, 7), (1, 8, 1), (16, 16, 3), (64, 8, 1024),
+                                   (1, 2, (1 << 27) + 6)])
 def test_transpose_outer_bit_exact(dtype, a, b, c):
     xs = inputs.complex_input((a, b, c), 41, "normal", dtype)
     x = to_device(xs, dtype)
