@@ -16,21 +16,24 @@ def _tree(tmp_path, files):
 
 
 def test_fingerprint_follows_kernel_sources(tmp_path, monkeypatch):
-    root = _tree(tmp_path, {"a.cu": "x", "b.cuh": "y", "c.h": "z", "notes.txt": "ignored"})
+    root = _tree(tmp_path, {"pass_kernels.cuh": "x", "pass_c32.cu": "y", "wsfft_api.cu": "z",
+                            "transpose.cu": "other kernel", "notes.txt": "ignored"})
     monkeypatch.setattr(bench, "ROOT", str(root))
+    csrc = root / "paper_2209_15040_gb300" / "csrc"
     h0 = bench.source_sha256()
-    (root / "paper_2209_15040_gb300" / "csrc" / "notes.txt").write_text("changed")
-    assert bench.source_sha256() == h0  # only .cu/.cuh/.h count
-    (root / "paper_2209_15040_gb300" / "csrc" / "b.cuh").write_text("y2")
+    (csrc / "notes.txt").write_text("changed")
+    (csrc / "transpose.cu").write_text("changed")
+    assert bench.source_sha256() == h0  # files outside the benchmark plan's kernels do not count
+    (csrc / "pass_c32.cu").write_text("y2")
     assert bench.source_sha256() != h0
-    (root / "paper_2209_15040_gb300" / "csrc" / "b.cuh").write_text("y")
+    (csrc / "pass_c32.cu").write_text("y")
     assert bench.source_sha256() == h0
-    (root / "paper_2209_15040_gb300" / "csrc" / "b2.cuh").write_text("")
-    assert bench.source_sha256() != h0  # a new file counts too
+    (csrc / "fft_core.cuh").write_text("")
+    assert bench.source_sha256() != h0  # a listed file that appears counts too
 
 
 def test_traffic_lookup_only_for_matching_sources(tmp_path, monkeypatch):
-    root = _tree(tmp_path, {"k.cu": "kernel"})
+    root = _tree(tmp_path, {"pass_kernels.cuh": "kernel"})
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.kernel_traffic(0) is None  # no record
     (root / "profiles").mkdir()
@@ -39,7 +42,7 @@ def test_traffic_lookup_only_for_matching_sources(tmp_path, monkeypatch):
     assert bench.kernel_traffic(0) == 1.5e9
     assert bench.kernel_traffic(2) == 2.0e9
     assert bench.kernel_traffic(1) is None  # not recorded
-    (root / "paper_2209_15040_gb300" / "csrc" / "k.cu").write_text("kernel, edited")
+    (root / "paper_2209_15040_gb300" / "csrc" / "pass_kernels.cuh").write_text("kernel, edited")
     assert bench.kernel_traffic(0) is None  # counters of older kernels are not reported
 
 
