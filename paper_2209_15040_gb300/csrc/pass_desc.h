@@ -45,6 +45,7 @@ struct PassArgs {
     int *status;        // plan's device status word (kernels with bounded waits)
     uint64_t timeout_ns;  // bound of each wait
     int no_pdl;         // 1: launch without programmatic dependent launch
+    int reverse;        // strided launches: 1 = blocks take the tiles from the last one down
 };
 
 // tile codes at or above this select the complex64 pencil-pair strided

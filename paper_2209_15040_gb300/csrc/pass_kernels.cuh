@@ -247,7 +247,8 @@ __global__ void __launch_bounds__(W *(N / E), strided_min_blocks(W *(N / E), E))
     pdl_enter();
     const int w = threadIdx.x % W;
     const int t = threadIdx.x / W;
-    const int64_t q = ((int64_t)blockIdx.x + a.tile0) * W + w;
+    const int64_t blk = a.reverse ? (int64_t)gridDim.x - 1 - blockIdx.x : (int64_t)blockIdx.x;
+    const int64_t q = (blk + a.tile0) * W + w;
     const int64_t o = q >> a.log_inner;
     const int64_t i = q & (a.inner - 1);
     const int64_t base = o * ((int64_t)N << a.log_inner) + i;
@@ -562,7 +563,8 @@ __global__ void __launch_bounds__((W / 2) * (N / E), strided_min_blocks((W / 2) 
     constexpr int WP = W / 2;
     const int wp = threadIdx.x % WP;
     const int t = threadIdx.x / WP;
-    const int64_t q = ((int64_t)blockIdx.x + a.tile0) * W + 2 * wp;  // first pencil of the pair
+    const int64_t blk = a.reverse ? (int64_t)gridDim.x - 1 - blockIdx.x : (int64_t)blockIdx.x;
+    const int64_t q = (blk + a.tile0) * W + 2 * wp;  // first pencil of the pair
     const int64_t o = q >> a.log_inner;
     const int64_t i = q & (a.inner - 1);
     const int64_t base = o * ((int64_t)N << a.log_inner) + i;   // element offset (even)

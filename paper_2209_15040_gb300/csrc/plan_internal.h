@@ -39,6 +39,7 @@ struct PassSpec {
     int64_t units;               // completion counters used (pass A)
     float c_scale, s_scale;      // pass A: scale after the contiguous / strided superstep
     bool no_pdl;                 // launch without programmatic dependent launch
+    bool reverse;                // strided: tiles taken from the last one down
 };
 
 struct Plan {

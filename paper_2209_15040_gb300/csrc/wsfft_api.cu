@@ -821,6 +821,13 @@ int Plan::build_schedule() {
     // tail (512^3 FP16: 0.752 ms per transform with it, 0.717 ms without)
     for (size_t i = 0; i < passes.size(); ++i)
         passes[i].no_pdl = i > 0 && passes[i - 1].kind == PASS_CONTIG && passes[i - 1].tile >= SPLIT_TILE;
+    // A strided superstep right after a contiguous one (the y superstep after
+    // z) takes its tiles from the last slab down: the contiguous pass wrote
+    // the last slabs last, and the first blocks then find them in L2
+    // (measured at 512^3: y 0.330 -> 0.323 ms, 973 -> 967 us per transform)
+    for (size_t i = 0; i < passes.size(); ++i)
+        passes[i].reverse = i > 0 && passes[i].kind == PASS_STRIDED && passes[i - 1].kind == PASS_CONTIG &&
+                            !passes[i].variant && !passes[i - 1].variant;
     for (auto &p : passes) {
         if (p.N > 4096 || !is_pow2(p.N)) return WSFFT_ERR_INVALID_SIZE;
         p.tw = p.tile == TC_TILE ? tc_table(p.N) : table(p.N, p.E);
@@ -959,6 +966,7 @@ PassArgs Plan::pass_args(const PassSpec &p, int64_t npencils) const {
     a.status = d_status;
     a.timeout_ns = (uint64_t)wait_timeout_ns;
     a.no_pdl = p.no_pdl ? 1 : 0;
+    a.reverse = p.reverse ? 1 : 0;
     return a;
 }
 
