@@ -205,6 +205,8 @@ cudaError_t launch_extra_variant(int kind, int N, int E, int tile, const void *i
         return launch_strided<1024, 32, 16, S, true>(in, out, a, st);
     if (kind == PASS_CONTIG && N == 1024 && E == 32 && tile == 8)
         return launch_contig<1024, 32, 8, S, true>(in, out, a, st);
+    if (kind == PASS_CONTIG && N == 512 && E == 32 && tile == 16)
+        return launch_contig<512, 32, 16, S, true>(in, out, a, st);
     return cudaErrorInvalidValue;
 }
 

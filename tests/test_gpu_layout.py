@@ -195,7 +195,7 @@ def _to_wafer(a):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("shape", [(2, 64, 128, 256), (1, 256, 64, 128), (1, 128, 512, 64)])
+@pytest.mark.parametrize("shape", [(2, 64, 128, 256), (1, 256, 64, 128), (1, 128, 512, 64), (2, 64, 64, 512)])
 @pytest.mark.parametrize("inplace", [False, True])
 def test_forward_wafer(dtype, shape, inplace):
     xs, xc = seeded(shape, 15, "uniform", dtype)
@@ -210,7 +210,7 @@ def test_forward_wafer(dtype, shape, inplace):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("shape", [(2, 64, 128, 256), (1, 128, 512, 64)])
+@pytest.mark.parametrize("shape", [(2, 64, 128, 256), (1, 128, 512, 64), (2, 512, 64, 64)])
 @pytest.mark.parametrize("inplace", [False, True])
 def test_inverse_from_wafer(dtype, shape, inplace):
     # the device buffer holds a spectrum X[k0][k1][k2] stored as [k2][k0][k1]

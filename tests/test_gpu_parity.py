@@ -107,7 +107,7 @@ def test_1d_short(n):
     check((3, n), 1, seed=9, direction=W.INVERSE)
 
 
-@pytest.mark.parametrize("n", [8192, 1 << 14, 1 << 16, 1 << 19, 1 << 20, 1 << 21, 1 << 24])
+@pytest.mark.parametrize("n", [8192, 1 << 14, 1 << 16, 1 << 17, 1 << 18, 1 << 19, 1 << 20, 1 << 21, 1 << 24])
 def test_1d_four_step(n):
     batch = max(1, (1 << 22) // n)
     check((batch, n), 1, seed=1)

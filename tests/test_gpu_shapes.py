@@ -169,6 +169,8 @@ def test_1024_shapes(dtype):
     (1 << 19, [(1, 32, 8)]),               # 1024 x 512: 1024-point contiguous superstep, transposed store
     (1 << 19, [(0, 32, 16), (1, 32, 8)]),  # and the 512-point strided one, 32 values per thread
     (1 << 20, [(0, 32, 16)]),              # complex64 2048 x 512, 16-bit storage 1024 x 1024
+    (1 << 18, []),                         # 512 x 512: 512-point contiguous superstep, 32 values x 16 pencils
+    (1 << 18, [(1, 8, 0)]),                # the same with the general 8 values x 16 pencils
 ])
 def test_four_step_shapes(dtype, n, settings):
     # 1D four-step split n = n1 (contiguous) x n2 (strided): pass 0 strided
