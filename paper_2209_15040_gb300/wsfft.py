@@ -168,9 +168,10 @@ class Plan:
                                                  int(tile)), "wsfft_plan_set_pass_variant")
 
     def set_engine(self, mode) -> None:
-        """Schedule of an n0 x n x n transform: 4 cluster-fused z and y per slab
-        (the default where it is built: n in {256, 512}), 0 one launch per
-        superstep, 3 warp-per-pencil, 1 persistent, 2 pipelined."""
+        """Schedule of an n0 x n x n transform: 0 one launch per superstep (the
+        default), 4 cluster-fused z and y per slab (n in {256, 512}),
+        3 warp-per-pencil, 1 persistent, 2 pipelined.  A mode the shape does not
+        support runs one launch per superstep."""
         _check(lib().wsfft_plan_set_engine(self._h, int(mode)), "wsfft_plan_set_engine")
 
     def set_wait_test(self, withhold: bool, timeout_ns: int) -> None:
