@@ -309,7 +309,8 @@ def sizes_leg(W, dev, stream, hbm_peak, steps=20, warmup=3):
     4096 x 4096 and 1D 2^20 x batch 512 (complex64).  GB/s counts one read and
     one write of the array per launch; the minimum-bytes fraction uses 2
     passes for 2D and 3D and 1 for 1D.  Arrays of 16 MiB (128^3) sit in L2:
-    no roofline claim there."""
+    no roofline claim there; those sizes are also timed replayed from a
+    captured CUDA graph."""
     cases = [((32, 32, 32), 1, W.C32, 8), ((128, 128, 128), 1, W.C32, 8), ((256, 256, 256), 1, W.C32, 8),
              ((1024, 1024, 1024), 1, W.C32, 8), ((1024, 1024, 1024), 1, W.C16F, 4),
              ((4096, 4096), 1, W.C32, 8), ((1 << 20,), 512, W.C32, 8)]
@@ -339,6 +340,10 @@ def sizes_leg(W, dev, stream, hbm_peak, steps=20, warmup=3):
             rec["min_bytes_roofline_frac"] = round(min_passes * 2 * nbytes / (hbm_peak * 1e9) / (us * 1e-6), 4)
         else:
             rec["note"] = "array fits in L2: no roofline claim"
+        if nbytes <= 16 * 2 ** 20:
+            # launch-bound sizes: the same pair replayed from a captured CUDA graph
+            gms = graph_pairs(f, i, xs, ys, steps, warmup)
+            rec["graph_us_per_transform"] = round(gms / steps * 1e3 / 2 / batch, 3)
         out.append(rec)
         f.close()
         i.close()
@@ -583,6 +588,35 @@ def timed_pairs(fwd, inv, x, y, steps, warmup, world, stream):
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def graph_pairs(fwd, inv, x, y, steps, warmup):
+    """The pair of timed_pairs captured once into a CUDA graph and replayed
+    `steps` times (CUDA events on the replaying stream): what a caller that
+    replays a captured transform pays, without the per-launch host cost."""
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fwd.execute(x.data_ptr(), y.data_ptr(), s)
+        inv.execute(y.data_ptr(), y.data_ptr(), s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        fwd.execute(x.data_ptr(), y.data_ptr())
+        inv.execute(y.data_ptr(), y.data_ptr())
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            graph.replay()
+        e1.record(s)
+    torch.cuda.synchronize()
+    del graph
     return e0.elapsed_time(e1)
 
 

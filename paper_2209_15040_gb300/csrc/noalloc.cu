@@ -26,7 +26,6 @@
 // the twiddle tables into their array on the caller's stream and waits for
 // that stream, looks up the arrays' device addresses with
 // cudaGetSymbolAddress and queries the occupancy of the persistent kernel.
-// Make that first call before any stream capture.
 //
 // Timeouts: pass A's waits are bounded (one second each); a wait that runs
 // out sets a status word in a third static array and its tile is skipped, so
