@@ -558,6 +558,8 @@ def run_case(args):
         x = torch.randn(dims + (2,), device="cuda").to(torch.float16 if code == W.C16F else torch.bfloat16)
     y = torch.empty_like(x)
     plan = W.Plan(dims, code, W.FORWARD, 1)
+    if args.case_layout != "natural":
+        plan.set_layout({"swapped": W.LAYOUT_SWAPPED, "wafer": W.LAYOUT_WAFER}[args.case_layout])
     if args.case_engine is not None:
         plan.set_engine(args.case_engine)
     if args.case_variant:
@@ -566,7 +568,7 @@ def run_case(args):
         plan.execute(x.data_ptr(), y.data_ptr())
     torch.cuda.synchronize()
     print(json.dumps({"case": list(dims), "dtype": args.case_dtype, "variant": args.case_variant,
-                      "engine": args.case_engine,
+                      "engine": args.case_engine, "layout": args.case_layout,
                       "passes": plan.passes()[0], "reps": args.case_reps, "status": plan.sync_status()}))
     plan.close()
 
@@ -641,6 +643,8 @@ def main():
     ap.add_argument("--case-dtype", default="c32", choices=["c32", "c16f", "c16bf"])
     ap.add_argument("--case-engine", type=int, default=None,
                     help="schedule of the case's plan (wsfft_plan_set_engine: 0..4)")
+    ap.add_argument("--case-layout", default="natural", choices=["natural", "swapped", "wafer"],
+                    help="spectral layout of the case's plan (wsfft_plan_set_layout)")
     ap.add_argument("--case-variant", default=None,
                     help="PASS,E,TILE: kernel shape of one pass (wsfft_plan_set_pass_variant)")
     ap.add_argument("--sweep", action="store_true",
