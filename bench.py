@@ -777,13 +777,22 @@ def main():
         esteps = max(2, min(args.steps, 10))
         torch.cuda.synchronize()
         barrier(world)
+        # each step timed on its own (host clock, synchronised: the copies of
+        # one step cannot overlap the next, whose input waits on them anyway);
+        # the median is the value, the mean and the extremes go beside it (the
+        # host link is shared with the machine's other work)
+        step_s = []
         t0 = time.perf_counter()
         for _ in range(esteps):
+            ts = time.perf_counter()
             fwd.execute_host(hx.data_ptr(), hy.data_ptr(), stream)
             inv.execute_host(hy.data_ptr(), hy.data_ptr(), stream)
-        torch.cuda.synchronize()
+            torch.cuda.synchronize()
+            step_s.append(time.perf_counter() - ts)
         barrier(world)
         dt = allmax(world, time.perf_counter() - t0)
+        med = allmax(world, statistics.median(step_s))
+        lo, hi = allmax(world, min(step_s)), allmax(world, max(step_s))
         # the host link as it ran during this leg (one 1 GiB copy each way,
         # the same pinned buffers): the floor the end-to-end number sits on
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -797,9 +806,12 @@ def main():
         nbytes = ELEMS * 8
         h2d = nbytes / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e9
         d2h = nbytes / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9
-        e2e = {"value": round(dt / esteps * 1e6 / 2 / world, 2), "unit": "us",
+        e2e = {"value": round(med * 1e6 / 2 / world, 2), "unit": "us",
                "h2d_bytes_per_step": 2 * ELEMS * 8, "d2h_bytes_per_step": 2 * ELEMS * 8,
-               "steps": esteps, "entry": "wsfft_execute_host (pinned host buffers)",
+               "steps": esteps, "statistic": "median of the per-step times",
+               "mean_us": round(dt / esteps * 1e6 / 2 / world, 2),
+               "min_us": round(lo * 1e6 / 2 / world, 2), "max_us": round(hi * 1e6 / 2 / world, 2),
+               "entry": "wsfft_execute_host (pinned host buffers)",
                "link_h2d_gbs": round(h2d, 1), "link_d2h_gbs": round(d2h, 1),
                "copy_floor_us": round((nbytes / h2d + nbytes / d2h) / 1e3, 1)}
 
