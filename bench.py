@@ -814,6 +814,28 @@ def main():
                "entry": "wsfft_execute_host (pinned host buffers)",
                "link_h2d_gbs": round(h2d, 1), "link_d2h_gbs": round(d2h, 1),
                "copy_floor_us": round((nbytes / h2d + nbytes / d2h) / 1e3, 1)}
+        del hx, hy
+        # beside it: one forward call on a batch of 4 arrays in pinned host
+        # memory, where the next array's copies in overlap the previous one's
+        # copies out (the two directions of the link)
+        if world == 1:
+            nb = 4
+            bx = torch.empty((nb,) + DIMS, dtype=torch.complex64).pin_memory()
+            for b in range(nb):
+                bx[b].copy_(x.cpu())
+            by = torch.empty_like(bx).pin_memory()
+            fb = W.Plan(DIMS, W.C32, W.FORWARD, nb)
+            fb.execute_host(bx.data_ptr(), by.data_ptr(), stream)
+            calls = []
+            for _ in range(3):
+                ts = time.perf_counter()
+                fb.execute_host(bx.data_ptr(), by.data_ptr(), stream)
+                calls.append(time.perf_counter() - ts)
+            fb.close()
+            e2e["batched"] = {"batch": nb, "direction": "forward",
+                              "us_per_transform": round(statistics.median(calls) / nb * 1e6, 2),
+                              "calls": len(calls), "statistic": "median of the calls, per transform"}
+            del bx, by
 
     sizes = None
     if not args.no_sizes and world == 1:

@@ -205,9 +205,11 @@ int wsfft_execute(wsfft_plan plan, const void *in, void *out, wsfft_stream strea
  * copies overlap the compute: slab chunks come in on a second stream (owned
  * by the plan) and are transformed along the last axis as they arrive, the
  * first axis is transformed over the whole array, and the middle axis slab
- * chunk by slab chunk, each chunk copied back as soon as it is done (the
- * result equals wsfft_execute's up to rounding: the axes are taken in
- * another order).  The first call allocates the device buffer
+ * chunk by slab chunk, each chunk copied back on a third stream (also the
+ * plan's) as soon as it is done; with batch > 1 the next transform's copies
+ * in run while the previous one's go out (the result equals wsfft_execute's
+ * up to rounding: the axes are taken in another order).  The first call
+ * allocates the device buffer
  * (batch * prod(dims) elements).  Errors: as wsfft_execute, plus ALLOC. */
 int wsfft_execute_host(wsfft_plan plan, const void *host_in, void *host_out,
                        wsfft_stream stream);

@@ -58,7 +58,8 @@ struct Plan {
     int64_t work_cap = 0;
     void *work = nullptr;
     void *host_buf = nullptr;  // device buffer for wsfft_execute_host
-    cudaStream_t copy_stream = nullptr;  // wsfft_execute_host: copies overlapping the supersteps
+    cudaStream_t copy_stream = nullptr;      // wsfft_execute_host: host-to-device copies overlapping the supersteps
+    cudaStream_t copy_out_stream = nullptr;  // and the device-to-host copies, on their own stream
     std::vector<cudaEvent_t> pipe_ev;
     int *d_status = nullptr;   // device status word (timeouts)
     cudaStream_t setup_st = nullptr;  // plan-owned stream for table uploads (synchronised per upload)

@@ -989,13 +989,15 @@ PassArgs Plan::pass_args(const PassSpec &p, int64_t npencils) const {
 // stream and the z superstep of each chunk (slab-local) runs as soon as the
 // chunk has arrived; the x superstep, which needs every slab, runs over the
 // whole array; then the y superstep (slab-local again) runs chunk by chunk
-// and each finished chunk goes back to the host with one contiguous copy
-// while the next is transformed.  The supersteps are taken in the order z, x,
-// y (the order of axes is free, Section 1).  The data crosses the host link
-// once in each direction; the x superstep and one chunk's z and y are the
-// only compute not hidden behind a copy.  (Chunking the x superstep instead
-// would need strided 2D copies back, measured 17% slower than contiguous
-// ones on this link.)
+// and each finished chunk goes back to the host with one contiguous copy, on
+// a third stream, while the next is transformed.  The supersteps are taken in
+// the order z, x, y (the order of axes is free, Section 1).  The data crosses
+// the host link once in each direction; the x superstep and one chunk's z
+// and y are the only compute of a lone transform not hidden behind a copy,
+// and in a batch the next transform's copies in share the time of the
+// previous one's copies out (the two directions of the link).  (Chunking the
+// x superstep instead would need strided 2D copies back, measured 17% slower
+// than contiguous ones on this link.)
 bool Plan::can_pipeline_host() const {
     if (ragged || rank != 3 || chunk != batch || passes.size() != 3 || dims[0] < 2) return false;
     if (passes[0].kind != PASS_CONTIG || passes[1].kind != PASS_STRIDED || passes[2].kind != PASS_STRIDED)
@@ -1007,14 +1009,25 @@ bool Plan::can_pipeline_host() const {
 
 int Plan::run_host_pipelined(const void *hin, void *hout, cudaStream_t st) {
     constexpr int K = 8;  // chunks per direction
-    if (!copy_stream) {
-        if (cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
-            copy_stream = nullptr;
-            return WSFFT_ERR_CUDA;
-        }
-        pipe_ev.resize(2 * K + 2);
-        for (auto &e : pipe_ev)
-            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return WSFFT_ERR_CUDA;
+    // streams and events are made on first use; a call that failed half-way
+    // through making them leaves nothing half-made for the next one
+    if (!copy_stream && cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        copy_stream = nullptr;
+        return WSFFT_ERR_CUDA;
+    }
+    if (!copy_out_stream && cudaStreamCreateWithFlags(&copy_out_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        copy_out_stream = nullptr;
+        return WSFFT_ERR_CUDA;
+    }
+    if (pipe_ev.size() != 2 * K + 2) {
+        std::vector<cudaEvent_t> evs(2 * K + 2, nullptr);
+        for (auto &e : evs)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                for (auto made : evs)
+                    if (made) cudaEventDestroy(made);
+                return WSFFT_ERR_CUDA;
+            }
+        pipe_ev.swap(evs);
     }
     const int64_t eb = elem_bytes(dtype);
     const int64_t n0 = dims[0], I = dims[1] * dims[2];
@@ -1022,12 +1035,19 @@ int Plan::run_host_pipelined(const void *hin, void *hout, cudaStream_t st) {
     cudaEvent_t ev_start = pipe_ev[2 * K], ev_done = pipe_ev[2 * K + 1];
     char *dev = (char *)host_buf;
     auto ck = [](cudaError_t e) { return e == cudaSuccess; };
+    // Both copy streams start after the work already on `st`.  Copies in run
+    // on copy_stream and copies out on copy_out_stream, so with a batch the
+    // next transform's chunks come in (one direction of the link) while the
+    // previous one's go out (the other): the transforms own disjoint parts of
+    // the device buffer and of the host buffers (also in place: transform b
+    // reads and writes only its own host slice).
+    if (!ck(cudaEventRecord(ev_start, st)) || !ck(cudaStreamWaitEvent(copy_stream, ev_start, 0)) ||
+        !ck(cudaStreamWaitEvent(copy_out_stream, ev_start, 0)))
+        return WSFFT_ERR_CUDA;
     for (int64_t b = 0; b < batch; ++b) {
         const char *hb = (const char *)hin + b * elems * eb;
         char *ho = (char *)hout + b * elems * eb;
         char *db = dev + b * elems * eb;
-        if (!ck(cudaEventRecord(ev_start, st)) || !ck(cudaStreamWaitEvent(copy_stream, ev_start, 0)))
-            return WSFFT_ERR_CUDA;
         auto run_pass = [&](const PassSpec &p, char *ptr, int64_t npencils) {
             const PassArgs a = pass_args(p, npencils);
             prof_begin(st);
@@ -1062,13 +1082,16 @@ int Plan::run_host_pipelined(const void *hin, void *hout, cudaStream_t st) {
             const int64_t o = s0 * I * eb, bytes = (s1 - s0) * I * eb;
             rc = run_pass(py, db + o, (s1 - s0) * dims[2]);
             if (rc != WSFFT_SUCCESS) return rc;
-            if (!ck(cudaEventRecord(pipe_ev[K + c], st)) || !ck(cudaStreamWaitEvent(copy_stream, pipe_ev[K + c], 0)) ||
-                !ck(cudaMemcpyAsync(ho + o, db + o, (size_t)bytes, cudaMemcpyDeviceToHost, copy_stream)))
+            if (!ck(cudaEventRecord(pipe_ev[K + c], st)) ||
+                !ck(cudaStreamWaitEvent(copy_out_stream, pipe_ev[K + c], 0)) ||
+                !ck(cudaMemcpyAsync(ho + o, db + o, (size_t)bytes, cudaMemcpyDeviceToHost, copy_out_stream)))
                 return WSFFT_ERR_CUDA;
         }
-        if (!ck(cudaEventRecord(ev_done, copy_stream)) || !ck(cudaStreamWaitEvent(st, ev_done, 0)))
-            return WSFFT_ERR_CUDA;
     }
+    // `st` ends after the last copy out (every copy in was waited for by a
+    // z superstep on `st`)
+    if (!ck(cudaEventRecord(ev_done, copy_out_stream)) || !ck(cudaStreamWaitEvent(st, ev_done, 0)))
+        return WSFFT_ERR_CUDA;
     return WSFFT_SUCCESS;
 }
 
@@ -1188,6 +1211,7 @@ int Plan::wait_own_work() {
     bool ok = true;
     for (auto &kv : done_ev) ok &= cudaEventSynchronize(kv.second) == cudaSuccess;
     if (copy_stream) ok &= cudaStreamSynchronize(copy_stream) == cudaSuccess;
+    if (copy_out_stream) ok &= cudaStreamSynchronize(copy_out_stream) == cudaSuccess;
     if (setup_st) ok &= cudaStreamSynchronize(setup_st) == cudaSuccess;
     return ok ? WSFFT_SUCCESS : WSFFT_ERR_CUDA;
 }
@@ -1215,8 +1239,10 @@ Plan::~Plan() {
     for (auto &kv : fs_tables) cudaFree(kv.second);
     if (work) cudaFree(work);
     if (host_buf) cudaFree(host_buf);
-    for (auto e : pipe_ev) cudaEventDestroy(e);
+    for (auto e : pipe_ev)
+        if (e) cudaEventDestroy(e);
     if (copy_stream) cudaStreamDestroy(copy_stream);
+    if (copy_out_stream) cudaStreamDestroy(copy_out_stream);
     if (d_status) cudaFree(d_status);
     for (auto &kv : done_ev) cudaEventDestroy(kv.second);
     if (setup_st) cudaStreamDestroy(setup_st);
