@@ -229,6 +229,55 @@ def cpu_sample_oracle(reps: int = 3):
     return rec, x, y_ref
 
 
+def _errs(got, ref):
+    """rel-L2 over all elements (re and im as reals), max-abs, max-abs over the
+    largest reference magnitude."""
+    d = got - ref
+    num = float(np.sqrt(np.sum(d.real ** 2 + d.imag ** 2)))
+    den = float(np.sqrt(np.sum(ref.real ** 2 + ref.imag ** 2)))
+    mabs = float(np.max(np.abs(d)))
+    return {"rel_l2": num / den, "max_abs": mabs, "max_abs_rel": mabs / float(np.max(np.abs(ref)))}
+
+
+def oracle_per_config(W, dev, stream, reps=3):
+    """Part of the CPU-baseline leg: the other configurations of the workload
+    family -- 32^3 (uniform[-1,1), seed 0), 128^3, 256^3, 2D 4096^2 and 1D 2^20
+    (N(0,1), seed 1; the 1D one on a batch of 2, the same kernels as batch 512)
+    -- each run once forward on the GPU and compared element by element with
+    the FP64 oracle's forward of the same bytes; the oracle's time per
+    transform (best of `reps`) on the host cores beside it."""
+    import oracle
+    from paper_2209_15040_gb300 import inputs
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    cases = [((32, 32, 32), 1, 0, "uniform"), ((128, 128, 128), 1, 1, "normal"),
+             ((256, 256, 256), 1, 1, "normal"), ((4096, 4096), 1, 1, "normal"),
+             ((1 << 20,), 2, 1, "normal")]
+    parity, times = [], []
+    for dims, batch, seed, dist in cases:
+        xs = inputs.complex_input((batch,) + dims, seed, dist, "c32")
+        xc = xs.astype(np.complex128)
+        xd = torch.from_numpy(np.ascontiguousarray(xs)).to(dev)
+        yd = torch.empty_like(xd)
+        p = W.Plan(dims, W.C32, W.FORWARD, batch)
+        p.execute(xd.data_ptr(), yd.data_ptr(), stream)
+        torch.cuda.synchronize()
+        p.close()
+        got = yd.cpu().numpy().astype(np.complex128)
+        best, ref = None, None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            ref = oracle.fftn(xc, rank=len(dims), sign=-1)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        e = _errs(got, ref)
+        parity.append({"dims": list(dims), "batch": batch, "rel_l2": e["rel_l2"], "max_abs": e["max_abs"],
+                       "max_abs_rel": e["max_abs_rel"]})
+        times.append({"dims": list(dims), "oracle_us_per_transform": round(best / batch * 1e6, 1),
+                      "sample": f"best of {reps} FP64 forwards of batch {batch}"})
+        del xd, yd
+    return parity, times
+
+
 def parity_512(W, x_c128, y_ref, dev, stream):
     """The GPU forward transform of the oracle's own 512^3 input, element by
     element against the FP64 oracle's forward: complex64 (paper
@@ -236,13 +285,7 @@ def parity_512(W, x_c128, y_ref, dev, stream):
     16-bit-rounded input with the orthonormal scaling."""
     import oracle
     from paper_2209_15040_gb300 import inputs
-
-    def errs(got, ref):
-        d = got - ref
-        num = float(np.sqrt(np.sum(d.real ** 2 + d.imag ** 2)))
-        den = float(np.sqrt(np.sum(ref.real ** 2 + ref.imag ** 2)))
-        mabs = float(np.max(np.abs(d)))
-        return {"rel_l2": num / den, "max_abs": mabs, "max_abs_rel": mabs / float(np.max(np.abs(ref)))}
+    errs = _errs
 
     out = {}
     xd = torch.from_numpy(x_c128.astype(np.complex64)).to(dev)
@@ -859,6 +902,9 @@ def main():
         cpu, x_or, y_or = cpu_sample_oracle()
         parity = parity_512(W, x_or, y_or, dev, stream)
         del x_or, y_or
+        cfg_parity, cfg_times = oracle_per_config(W, dev, stream)
+        parity["per_config"] = cfg_parity
+        cpu["per_config"] = cfg_times
 
     if rank == 0:
         line = {
