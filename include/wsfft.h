@@ -32,7 +32,8 @@
  *  - Pointers passed to execute are device pointers (unless named host_*),
  *    owned by the caller, 16-byte aligned, and must stay valid until the
  *    enqueued work completes.  in == out (in place) is allowed; otherwise in
- *    and out must not overlap.  `in` is never written when in != out.
+ *    and out must not overlap (a partial overlap of the two arrays returns
+ *    WSFFT_ERR_INVALID_ARG).  `in` is never written when in != out.
  *  - Streams are cudaStream_t values passed as wsfft_stream (NULL = the legacy
  *    default stream).  Execute calls are asynchronous on that stream.  The
  *    one-launch-per-superstep kernels of arrays up to 2 GiB are launched with
@@ -341,12 +342,12 @@ int wsfft_plan_launch_times(wsfft_plan plan, float *ms, int capacity, int *count
  * counters (16 KiB) and twiddle tables (16 KiB) live in static device arrays
  * that every GPU loading the library keeps until the process exits.
  *   n: 128, 256 or 512; batch * n <= 4096.  Larger sizes return
- *   WSFFT_ERR_INVALID_SIZE; null or misaligned pointers and bad directions
- *   return WSFFT_ERR_INVALID_ARG.
+ *   WSFFT_ERR_INVALID_SIZE; null or misaligned pointers, in and out that
+ *   share bytes without being equal, and bad directions return
+ *   WSFFT_ERR_INVALID_ARG.
  * The first call on each device does that device's set-up (table upload on
  * `stream`, which it then synchronises, symbol lookup, occupancy query) with
- * the device current.  All calls on a
- * device share the scratch array, which keeps the last call's contents (each
+ * the device current.  All calls on a device share the scratch array, which keeps the last call's contents (each
  * call clears the counters it uses): calls that overlap on the GPU race and
  * must not be made.  A bounded device-side wait that runs out leaves that
  * call's output incomplete and is reported only by

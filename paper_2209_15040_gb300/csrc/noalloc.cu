@@ -241,6 +241,13 @@ extern "C" int wsfft_execute_cube_noalloc(const void *in, void *out, int64_t n, 
         if (kShapes[i].n == n) s = i;
     if (s < 0 || batch < 1) return WSFFT_ERR_INVALID_SIZE;
     if (batch * n > kMaxSlabs) return WSFFT_ERR_INVALID_SIZE;  // counter array too small
+    {
+        // in == out is the in-place form; any other shared bytes would be
+        // read after another tile wrote them
+        const char *a = static_cast<const char *>(in), *b = static_cast<const char *>(out);
+        const size_t bytes = (size_t)(batch * n * n * n) * sizeof(float2);
+        if (a != b && a < b + bytes && b < a + bytes) return WSFFT_ERR_INVALID_ARG;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return WSFFT_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return WSFFT_ERR_UNSUPPORTED;

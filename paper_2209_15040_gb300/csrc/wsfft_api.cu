@@ -198,6 +198,12 @@ cudaError_t launch(int dtype, const PassSpec &p, const void *in, void *out, cons
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? WSFFT_SUCCESS : WSFFT_ERR_CUDA; }
 
+// two buffers of `bytes` that share some bytes without being the same buffer
+bool partial_overlap(const void *a, const void *b, size_t bytes) {
+    const char *x = static_cast<const char *>(a), *y = static_cast<const char *>(b);
+    return x != y && x < y + bytes && y < x + bytes;
+}
+
 }  // namespace
 
 namespace wsfft {
@@ -1396,6 +1402,7 @@ int wsfft_execute(wsfft_plan plan, const void *in, void *out, wsfft_stream strea
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || p->ragged || !in || !out) return WSFFT_ERR_INVALID_ARG;
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return WSFFT_ERR_INVALID_ARG;
+    if (partial_overlap(in, out, (size_t)(p->batch * p->elems * elem_bytes(p->dtype)))) return WSFFT_ERR_INVALID_ARG;
     const int rc = p->run(in, out, (cudaStream_t)stream);
     p->mark_done((cudaStream_t)stream);
     return rc;
@@ -1405,6 +1412,7 @@ int wsfft_execute_host(wsfft_plan plan, const void *host_in, void *host_out, wsf
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || p->ragged || !host_in || !host_out) return WSFFT_ERR_INVALID_ARG;
     const size_t bytes = (size_t)(p->batch * p->elems * elem_bytes(p->dtype));
+    if (partial_overlap(host_in, host_out, bytes)) return WSFFT_ERR_INVALID_ARG;
     if (!p->host_buf) {
         if (cudaMalloc(&p->host_buf, bytes) != cudaSuccess) {
             p->host_buf = nullptr;

@@ -199,3 +199,28 @@ def test_execute_rejects_misaligned_pointers():
         plan.execute(x.data_ptr() + 8, x.data_ptr())
     assert e.value.status == W.ERR_INVALID_ARG
     plan.close()
+
+
+def test_execute_rejects_partially_overlapping_buffers():
+    # in == out is the in-place form; arrays that share some bytes are refused
+    # (device and host entry points alike) and leave the data untouched
+    n = 16 * 16 * 16
+    plan = W.Plan((16, 16, 16), W.C32, W.FORWARD, 1)
+    x = torch.arange(2 * n, dtype=torch.float32, device="cuda").view(torch.complex64)
+    before = x.clone()
+    for shift in (2, n // 2, n - 2):  # 16-byte aligned shifts that overlap
+        with pytest.raises(W.WsfftError) as e:
+            plan.execute(x.data_ptr(), x.data_ptr() + 8 * shift)
+        assert e.value.status == W.ERR_INVALID_ARG
+        with pytest.raises(W.WsfftError) as e:
+            plan.execute(x.data_ptr() + 8 * shift, x.data_ptr())
+        assert e.value.status == W.ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert torch.equal(x, before)
+    plan.execute(x.data_ptr(), x.data_ptr() + 8 * n)  # adjacent, not overlapping
+    h = torch.zeros(2 * n, dtype=torch.complex64).pin_memory()
+    with pytest.raises(W.WsfftError) as e:
+        plan.execute_host(h.data_ptr(), h.data_ptr() + 8 * (n // 2))
+    assert e.value.status == W.ERR_INVALID_ARG
+    plan.close()
+    torch.cuda.synchronize()

@@ -99,3 +99,7 @@ def test_noalloc_rejects_sizes_beyond_its_arrays(lib):
     assert noalloc(lib, x, x, 1024, 1, W.FORWARD) == W.ERR_INVALID_SIZE
     assert noalloc(lib, x, x, 100, 1, W.FORWARD) == W.ERR_INVALID_SIZE
     assert noalloc(lib, x, x, 128, 1, 0) == W.ERR_INVALID_ARG
+    # in and out sharing bytes without being equal: refused before any GPU work
+    p = x.data_ptr()
+    assert lib.wsfft_execute_cube_noalloc(ctypes.c_void_p(p), ctypes.c_void_p(p + 16), 128, 1, W.FORWARD,
+                                          _stream()) == W.ERR_INVALID_ARG
