@@ -208,6 +208,47 @@ def test_1024cubed_forward_elementwise():
     inv.close()
 
 
+def test_1024cubed_fp16_forward_elementwise():
+    # full-size 1024^3 in FP16 storage (4 GiB: element offsets up to 2^30 at
+    # 4 bytes each, through the 16-bit instantiations of the 1024-point
+    # supersteps): every output element against the FP64 oracle of the
+    # FP16-rounded input under the orthonormal scaling
+    n = 1024
+    if _host_bytes() < (64 << 30):
+        pytest.skip("host memory below 64 GiB: the FP64 oracle of 1024^3 does not fit")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(12)
+    x = (torch.rand(n, n, n, 2, generator=g, device="cuda") * 2 - 1).to(torch.float16)
+    y = torch.empty_like(x)
+    fwd = W.Plan((n, n, n), W.C16F, W.FORWARD, 1)
+    fwd.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    assert fwd.sync_status() == W.SUCCESS
+    fwd.close()
+    xs = x.cpu().numpy()
+    del x
+    xc = np.empty((n, n, n), dtype=np.complex128)
+    for p0 in range(0, n, 64):
+        blk = xs[p0:p0 + 64].astype(np.float64)
+        xc[p0:p0 + 64] = blk[..., 0] + 1j * blk[..., 1]
+    del xs
+    got = y.cpu().numpy()
+    del y
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    ref = oracle.fftn(xc, norm=oracle.NORM_ORTHO)
+    del xc
+    num = den = mabs = 0.0
+    for p0 in range(0, n, 64):
+        blk = got[p0:p0 + 64].astype(np.float64)
+        d = (blk[..., 0] + 1j * blk[..., 1]) - ref[p0:p0 + 64]
+        num += float(np.sum(d.real ** 2 + d.imag ** 2))
+        den += float(np.sum(ref[p0:p0 + 64].real ** 2 + ref[p0:p0 + 64].imag ** 2))
+        mabs = max(mabs, float(np.max(np.abs(d))))
+    err = float(np.sqrt(num / den))
+    print(f"1024^3 FP16 element-wise rel_l2 {err:.3e} max_abs {mabs:.3e}")
+    assert err < TOL["c16f"]
+
+
 @pytest.mark.parametrize("mode", [1, 3, 4])
 @pytest.mark.parametrize("shape", [(64, 512, 512), (32, 128, 128), (256, 256, 256), (2, 512, 512)])
 def test_fused_schedule_any_outer_axis(mode, shape):
