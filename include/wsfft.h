@@ -248,7 +248,10 @@ int wsfft_execute_ragged(wsfft_plan plan, const void *const *in, void *const *ou
  * ragged plan the candidates are the tile shape of each axis length that
  * occurs and the queue lag (wsfft_plan_set_ragged_variant), the key holds
  * the sorted multiset of instance shapes, and a ragged plan created later
- * with the same key takes the cached choice.
+ * with the same key takes the cached choice.  A cached entry that does not
+ * describe a schedule this build can launch (an unknown schedule, values out
+ * of range, a kernel shape that is not instantiated) is ignored: plan
+ * creation keeps the default schedule and wsfft_autotune times afresh.
  * Errors: ALLOC, CUDA. */
 int wsfft_autotune(wsfft_plan plan, wsfft_stream stream);
 

@@ -105,11 +105,26 @@ void save(const std::string &key, const Choice &c, double us) {
     fclose(f);
 }
 
+// Apply a choice (a candidate, or one read back from the cache file, whose
+// contents are not trusted): values out of range, or a shape no kernel is
+// instantiated for, leave the plan as it was and return an error.
 int apply(Plan &p, const Choice &c) {
+    if (c.mode < 0 || c.mode > 4) return WSFFT_ERR_INVALID_ARG;
+    for (auto &v : c.variants)
+        if (v[0] < 0 || v[1] < 1 || v[1] > 32 || (v[1] & (v[1] - 1)) || v[2] < 0) return WSFFT_ERR_INVALID_ARG;
+    const int old_mode = p.engine_mode;
+    const auto old_over = p.overrides;
     p.engine_mode = c.mode;
     p.overrides.clear();
     for (auto &v : c.variants) p.overrides[v[0]] = std::make_pair(v[1], v[2]);
-    return p.build_schedule();
+    int rc = p.build_schedule();
+    if (rc == WSFFT_SUCCESS && !p.overrides_launchable()) rc = WSFFT_ERR_UNSUPPORTED;
+    if (rc != WSFFT_SUCCESS) {
+        p.engine_mode = old_mode;
+        p.overrides = old_over;
+        p.build_schedule();
+    }
+    return rc;
 }
 
 // mean microseconds per execute, or a negative value if the schedule fails
@@ -216,7 +231,9 @@ double time_ragged(Plan &p, const std::vector<const void *> &in, const std::vect
 int autotune_ragged(Plan &p, cudaStream_t st) {
     const std::string key = ragged_key(p);
     Choice cached;
-    if (load(key, cached)) return apply_ragged(p, cached);
+    // a cached choice that does not apply (out of range for this build) is
+    // timed afresh
+    if (load(key, cached) && apply_ragged(p, cached) == WSFFT_SUCCESS) return WSFFT_SUCCESS;
     const size_t eb = p.dtype == WSFFT_C32 ? 8 : 4;
     const size_t bytes = (size_t)p.elems * eb;
     char *in = nullptr, *out = nullptr;
@@ -303,7 +320,9 @@ extern "C" int wsfft_autotune(wsfft_plan plan, wsfft_stream stream) {
     if (p->ragged) return autotune_ragged(*p, (cudaStream_t)stream);
     const std::string key = plan_key(*p);
     Choice cached;
-    if (load(key, cached)) return apply(*p, cached);
+    // a cached choice that does not apply (out of range, or a shape this
+    // build does not instantiate) is timed afresh
+    if (load(key, cached) && apply(*p, cached) == WSFFT_SUCCESS) return WSFFT_SUCCESS;
 
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)(p->batch * p->elems * (p->dtype == WSFFT_C32 ? 8 : 4));

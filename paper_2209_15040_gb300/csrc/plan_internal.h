@@ -100,6 +100,7 @@ struct Plan {
     std::map<int64_t, float2 *> fs_tables;        // four-step twiddle tables per long length
     const float2 *fourstep_table(int64_t L, int shift);
     int build_schedule();
+    bool overrides_launchable() const;  // every pass-shape override names an instantiated kernel
     int build_engine(int64_t n0, int64_t n, bool inv);
     int build_slab(int64_t n0, int64_t n, bool inv);
     int rag_build();                   // ragged plans: instance records and tile queue

@@ -198,6 +198,14 @@ cudaError_t launch(int dtype, const PassSpec &p, const void *in, void *out, cons
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? WSFFT_SUCCESS : WSFFT_ERR_CUDA; }
 
+// a pass-shape override the schedule builder may apply: a power-of-two count
+// of values per thread within the pencil (the builder makes twiddle tables for
+// it) and a non-negative tile code; whether a kernel of that shape exists is
+// checked separately (Plan::overrides_launchable)
+bool override_usable(int E, int tile, int N) {
+    return E >= 1 && E <= 32 && E <= N && (E & (E - 1)) == 0 && tile >= 0;
+}
+
 // two buffers of `bytes` that share some bytes without being the same buffer
 bool partial_overlap(const void *a, const void *b, size_t bytes) {
     const char *x = static_cast<const char *>(a), *y = static_cast<const char *>(b);
@@ -377,7 +385,8 @@ int Plan::build_engine(int64_t n0, int64_t n, bool inv) {
     passes.push_back(a);
     passes.push_back(b);
     for (auto &kv : overrides) {
-        if (kv.first < (int)passes.size() && passes[kv.first].kind == PASS_STRIDED) {
+        if (kv.first < (int)passes.size() && passes[kv.first].kind == PASS_STRIDED &&
+            override_usable(kv.second.first, kv.second.second, passes[kv.first].N)) {
             passes[kv.first].E = kv.second.first;
             passes[kv.first].tile = kv.second.second;
         }
@@ -457,7 +466,7 @@ int Plan::build_slab(int64_t n0, int64_t n, bool inv) {
     passes.push_back(a);
     passes.push_back(b);
     for (auto &kv : overrides)
-        if (kv.first == 1) {
+        if (kv.first == 1 && override_usable(kv.second.first, kv.second.second, passes[1].N)) {
             passes[1].E = kv.second.first;
             passes[1].tile = kv.second.second;
         }
@@ -831,7 +840,8 @@ int Plan::build_schedule() {
     }
     for (auto &kv : overrides) {
         if (kv.first < (int)passes.size() &&
-            (passes[kv.first].kind == PASS_CONTIG || passes[kv.first].kind == PASS_STRIDED)) {
+            (passes[kv.first].kind == PASS_CONTIG || passes[kv.first].kind == PASS_STRIDED) &&
+            override_usable(kv.second.first, kv.second.second, passes[kv.first].N)) {
             passes[kv.first].E = kv.second.first;
             passes[kv.first].tile = kv.second.second;
         }
@@ -868,6 +878,18 @@ int Plan::build_schedule() {
         work_cap = work_elems;
     }
     return WSFFT_SUCCESS;
+}
+
+bool Plan::overrides_launchable() const {
+    for (const auto &kv : overrides) {
+        if (kv.first < 0 || kv.first >= (int)passes.size()) return false;
+        const PassSpec &ps = passes[kv.first];
+        if (ps.E != kv.second.first || ps.tile != kv.second.second) return false;  // not applied
+        PassArgs a{};
+        a.npencils = 0;  // an empty launch returns before running
+        if (launch(dtype, ps, nullptr, nullptr, a, 0) == cudaErrorInvalidValue) return false;
+    }
+    return true;
 }
 
 int Plan::run(const void *in, void *out, cudaStream_t st) {

@@ -52,6 +52,42 @@ def test_autotune_cube_and_cache(tmp_path, monkeypatch):
     plan2.close()
 
 
+@pytest.mark.parametrize("bad", [
+    {"mode": 99, "variants": []},                      # no such schedule
+    {"mode": 0, "variants": [[0, 0, 8]]},              # zero values per thread
+    {"mode": 0, "variants": [[0, 16, 12345]]},         # a tile no kernel is instantiated for
+    {"mode": 0, "variants": [[2, 64, 16]]},            # more values per thread than a pencil holds
+    {"mode": 0, "variants": [[7, 16, 8]]},             # a pass the plan does not have
+])
+def test_cache_entries_that_do_not_hold_are_ignored(tmp_path, monkeypatch, bad):
+    # the cache file is outside the library's control (stale from another
+    # build, edited, corrupted): an entry that does not describe a launchable
+    # schedule leaves the plan on its default schedule, which still computes
+    # the transform
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("WSFFT_TUNE_CACHE", str(cache))
+    n = 64
+    plan = W.Plan((n, n, n), W.C32, W.FORWARD, 1)
+    npass = plan.passes()[0]
+    plan.autotune()
+    plan.close()
+    key = json.loads(cache.read_text().strip().splitlines()[0])["key"]
+    entry = {"key": key, "mode": bad["mode"], "variants": bad["variants"], "us": 1.0}
+    cache.write_text(json.dumps(entry) + "\n")
+    xs = inputs.complex_input((n, n, n), 2, "normal", "c32")
+    x = torch.from_numpy(xs).cuda()
+    y = torch.empty_like(x)
+    plan = W.Plan((n, n, n), W.C32, W.FORWARD, 1)
+    assert plan.passes()[0] == npass
+    plan.execute(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    assert plan.sync_status() == W.SUCCESS
+    assert oracle.rel_l2(y.cpu().numpy(), oracle.fftn(xs.astype(np.complex128))) < 5e-6
+    plan.autotune()  # the bad entry is not taken: autotune times and appends a good one
+    assert len(cache.read_text().strip().splitlines()) == 2
+    plan.close()
+
+
 def test_autotune_2d_without_cache(monkeypatch):
     monkeypatch.delenv("WSFFT_TUNE_CACHE", raising=False)
     xs = inputs.complex_input((2, 512, 256), 3, "normal", "c32")
