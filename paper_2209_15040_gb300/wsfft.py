@@ -11,6 +11,7 @@ Tensors:
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import os
 import threading
@@ -290,18 +291,53 @@ def storage_of(x: torch.Tensor):
     raise TypeError(f"unsupported dtype {x.dtype}")
 
 
-_plans: dict = {}
+_plans: "collections.OrderedDict" = collections.OrderedDict()
 _plans_lock = threading.Lock()
+_plan_cache_size = 32
+
+
+def set_plan_cache_size(n: int) -> None:
+    """Plans that fftn/ifftn keep (least recently used ones are destroyed
+    beyond it: a plan holds its tables and, for long 1D axes or the other
+    spectral layouts, a workspace of up to 4 GiB)."""
+    global _plan_cache_size
+    if n < 1:
+        raise ValueError("the plan cache holds at least one plan")
+    with _plans_lock:
+        _plan_cache_size = int(n)
+        _evict_locked()
+
+
+def clear_plan_cache() -> None:
+    """Destroy every plan fftn/ifftn keep (each waits for its own work)."""
+    with _plans_lock:
+        while _plans:
+            _plans.popitem(last=False)[1].close()
+
+
+def _evict_locked() -> None:
+    while len(_plans) > _plan_cache_size:
+        _plans.popitem(last=False)[1].close()
+
+
+def _get_plan_locked(dims, dtype, direction, batch, norm) -> Plan:
+    key = (torch.cuda.current_device(), tuple(dims), dtype, direction, batch, norm)
+    p = _plans.get(key)
+    if p is None:
+        p = Plan(dims, dtype, direction, batch, norm)
+        _plans[key] = p
+        _evict_locked()
+    else:
+        _plans.move_to_end(key)
+    return p
 
 
 def get_plan(dims, dtype, direction, batch, norm) -> Plan:
-    key = (torch.cuda.current_device(), tuple(dims), dtype, direction, batch, norm)
+    """The cached plan for these parameters (made on first use).  It may be
+    destroyed once more than the cache size of other plans have been used
+    since; fftn/ifftn enqueue their executes while holding the cache."""
     with _plans_lock:
-        p = _plans.get(key)
-        if p is None:
-            p = Plan(dims, dtype, direction, batch, norm)
-            _plans[key] = p
-        return p
+        return _get_plan_locked(dims, dtype, direction, batch, norm)
 
 
 def _run(x: torch.Tensor, rank, direction: int, norm, out=None) -> torch.Tensor:
@@ -323,9 +359,10 @@ def _run(x: torch.Tensor, rank, direction: int, norm, out=None) -> torch.Tensor:
         out = torch.empty_like(x)
     if x.numel() == 0:
         return out
-    with torch.cuda.device(x.device):
-        plan = get_plan(dims, code, direction, batch, norm)
-        plan.execute(x.data_ptr(), out.data_ptr())
+    with torch.cuda.device(x.device), _plans_lock:
+        # enqueue under the cache lock: no other thread can evict the plan
+        # between the lookup and the execute
+        _get_plan_locked(dims, code, direction, batch, norm).execute(x.data_ptr(), out.data_ptr())
     return out
 
 

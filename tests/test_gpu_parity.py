@@ -224,3 +224,46 @@ def test_execute_rejects_partially_overlapping_buffers():
     assert e.value.status == W.ERR_INVALID_ARG
     plan.close()
     torch.cuda.synchronize()
+
+
+# -- plans kept by fftn / ifftn ---------------------------------------------------
+
+def test_fftn_plan_cache_is_bounded_and_thread_safe():
+    import threading
+    W.clear_plan_cache()
+    W.set_plan_cache_size(3)
+    try:
+        sizes = (8, 16, 32, 64, 128)
+        for n in sizes:
+            xs, xc = seeded((4, n), 90 + n, "normal", "c32")
+            y = W.fftn(torch.from_numpy(xs).cuda(), rank=1)
+            assert oracle.rel_l2(y.cpu().numpy(), oracle.fftn(xc, rank=1)) < TOL["c32"]
+            assert len(W._plans) <= 3
+        assert len(W._plans) == 3
+        # two threads cycling through more shapes than the cache holds: every
+        # execute is enqueued while its plan is held, so none runs on a
+        # destroyed plan
+        errors = []
+
+        def worker(seed):
+            try:
+                for k in range(20):
+                    n = sizes[(seed + k) % len(sizes)]
+                    xs, xc = seeded((2, n), seed * 100 + k, "normal", "c32")
+                    y = W.ifftn(W.fftn(torch.from_numpy(xs).cuda(), rank=1), rank=1)
+                    torch.cuda.synchronize()
+                    if oracle.rel_l2(y.cpu().numpy(), xc) > TOL["c32"]:
+                        errors.append((seed, k, n))
+            except Exception as e:  # reported below
+                errors.append(repr(e))
+
+        threads = [threading.Thread(target=worker, args=(s,)) for s in (1, 2)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        assert not errors, errors
+        assert len(W._plans) <= 3
+    finally:
+        W.set_plan_cache_size(32)
+        W.clear_plan_cache()
