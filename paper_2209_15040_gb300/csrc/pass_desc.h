@@ -44,7 +44,6 @@ struct PassArgs {
     int64_t tile0;      // strided launches: index of the first tile (set by the launcher)
     int *status;        // plan's device status word (kernels with bounded waits)
     uint64_t timeout_ns;  // bound of each wait
-    int no_pdl;         // 1: launch without programmatic dependent launch
     int reverse;        // strided launches: 1 = blocks take the tiles from the last one down
 };
 

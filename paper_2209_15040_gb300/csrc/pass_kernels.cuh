@@ -538,12 +538,17 @@ struct ContigSplitAcc {
     __device__ __forceinline__ void after_load() const {}
 };
 
-// P pencils per block as P/2 split-form pairs
+// P pencils per block as P/2 split-form pairs.  Unlike the other superstep
+// kernels, a block lets the next kernel start launching only after its own
+// stores: the next kernel's blocks, arriving while this kernel's last wave
+// ran, slowed it (512^3 FP16 step 750 us with the early signal, 713 us with
+// no programmatic dependent launch after this kernel at all, 711 us with
+// the signal after the stores)
 template <int N, int E, int P, class S, bool PLAIN>
 __global__ void __launch_bounds__((P / 2) * (N / E))
     contig_split_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
     extern __shared__ float4 qsmem[];
-    pdl_enter();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     constexpr int T = N / E;
     const int t = threadIdx.x % T;
     const int pp = threadIdx.x / T;
@@ -551,6 +556,7 @@ __global__ void __launch_bounds__((P / 2) * (N / E))
     ContigSplitAcc<S, PLAIN, (T <= 32)> acc{in + q * N, out + q * N, qsmem + pp * contig_PS(N), N,
                                             a.conj_in, a.sx, a.sy, q < a.npencils, q + 1 < a.npencils};
     pencil_fft<N, E>(acc, t, a.tw);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // SPLIT selects the split-form accessor (packed FP32x2 butterflies)

@@ -28,7 +28,7 @@ inline bool plain_pass(const PassArgs &a) { return a.conj_in == 1.f && a.sx == 1
 // and 5% at 256^3, but 14% slower at 1024^3 (8 GiB), so larger passes
 // launch plainly.
 inline bool pdl_pass(const PassArgs &a, int N, int elem_bytes) {
-    return !a.no_pdl && a.npencils * (int64_t)N * elem_bytes <= ((int64_t)2 << 30);
+    return a.npencils * (int64_t)N * elem_bytes <= ((int64_t)2 << 30);
 }
 template <class... KArgs, class... Args>
 cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), unsigned grid, unsigned block, int smem,

@@ -38,7 +38,6 @@ struct PassSpec {
     int nitems;
     int64_t units;               // completion counters used (pass A)
     float c_scale, s_scale;      // pass A: scale after the contiguous / strided superstep
-    bool no_pdl;                 // launch without programmatic dependent launch
     bool reverse;                // strided: tiles taken from the last one down
 };
 

@@ -846,11 +846,6 @@ int Plan::build_schedule() {
             passes[kv.first].tile = kv.second.second;
         }
     }
-    // a launch right after a split-form contiguous launch goes without
-    // programmatic dependent launch: its early blocks slowed that kernel's
-    // tail (512^3 FP16: 0.752 ms per transform with it, 0.717 ms without)
-    for (size_t i = 0; i < passes.size(); ++i)
-        passes[i].no_pdl = i > 0 && passes[i - 1].kind == PASS_CONTIG && passes[i - 1].tile >= SPLIT_TILE;
     // A strided superstep right after a contiguous one (the y superstep after
     // z) takes its tiles from the last slab down: the contiguous pass wrote
     // the last slabs last, and the first blocks then find them in L2
@@ -923,7 +918,7 @@ int Plan::run(const void *in, void *out, cudaStream_t st) {
                 sa.tw_z = p.tw;
                 sa.tw_y = p.tw2;
                 const int64_t nslabs = p.units * nb;
-                const bool pdl = !p.no_pdl && nslabs * (int64_t)p.N * p.N * eb <= ((int64_t)2 << 30);
+                const bool pdl = nslabs * (int64_t)p.N * p.N * eb <= ((int64_t)2 << 30);
                 prof_begin(st);
                 cudaError_t e = launch_slab(dtype, p.N, (const char *)in + off, (char *)out + off, nslabs, sa, pdl,
                                             st, nullptr);
@@ -1007,7 +1002,6 @@ PassArgs Plan::pass_args(const PassSpec &p, int64_t npencils) const {
     a.tw_mask = p.twid_len ? (int)(p.twid_len - 1) : 0;
     a.status = d_status;
     a.timeout_ns = (uint64_t)wait_timeout_ns;
-    a.no_pdl = p.no_pdl ? 1 : 0;
     a.reverse = p.reverse ? 1 : 0;
     return a;
 }
@@ -1098,10 +1092,6 @@ int Plan::run_host_pipelined(const void *hin, void *hout, cudaStream_t st) {
         PassSpec px = passes[2], py = passes[1];
         py.conj_out = px.conj_out;
         px.conj_out = false;
-        // launch order here is z, x, y: the rule on programmatic dependent
-        // launch after a split-form contiguous launch follows that order
-        px.no_pdl = passes[0].kind == PASS_CONTIG && passes[0].tile >= SPLIT_TILE;
-        py.no_pdl = false;
         int rc = run_pass(px, db, I);
         if (rc != WSFFT_SUCCESS) return rc;
         // out: the y superstep of each slab chunk, then its copy back
