@@ -135,7 +135,17 @@ template <int N, int E, int P, class S, bool TRANS, bool PLAIN = false>
 __global__ void __launch_bounds__(P *(N / E))
     contig_kernel(const S *__restrict__ in, S *__restrict__ out, PassArgs a) {
     extern __shared__ float2 smem[];
-    pdl_enter();
+    // Pencils of up to 512 points stored in place let the next kernel start
+    // launching only after their stores (measured, complex64: 512^3 step
+    // 967.4 -> 964.9 us, 128^3 19.7 -> 19.2 us, 256^3 unchanged); the
+    // transposing and 1024-point variants keep the early signal (with the
+    // late one the 1D 2^20 four-step lost 0.5%, 1024^3 0.5%)
+    constexpr bool late_signal = !TRANS && N <= 512;
+    if constexpr (late_signal) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+    } else {
+        pdl_enter();
+    }
     constexpr int T = N / E;
     const int t = threadIdx.x % T;
     const int p = threadIdx.x / T;
@@ -188,6 +198,7 @@ __global__ void __launch_bounds__(P *(N / E))
             }
         }
     }
+    if constexpr (late_signal) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 template <class S, bool TWID, int LOP, int SOP, int W, bool PLAIN = false>
