@@ -39,21 +39,30 @@ def test_c_client_compiles_and_links(tmp_path):
     assert os.path.exists(exe)
 
 
+CODES = {"c32": 0, "c16f": 1, "c16bf": 2}
+TOLS = {"c32": 5e-6, "c16f": 3e-3, "c16bf": 2e-2}
+
+
 @pytest.mark.gpu
-@pytest.mark.parametrize("dims,batch,direction", [((64, 32, 16), 2, -1), ((1 << 14,), 3, 1), ((128, 256), 1, -1),
-                                                  ((512, 512, 512), 1, -1)])
-def test_c_client_matches_oracle(tmp_path, dims, batch, direction):
+@pytest.mark.parametrize("dims,batch,direction,dtype", [((64, 32, 16), 2, -1, "c32"), ((1 << 14,), 3, 1, "c32"),
+                                                        ((128, 256), 1, -1, "c32"), ((512, 512, 512), 1, -1, "c32"),
+                                                        ((64, 64, 64), 2, -1, "c16f"), ((128, 512), 1, 1, "c16bf")])
+def test_c_client_matches_oracle(tmp_path, dims, batch, direction, dtype):
     import oracle
     from paper_2209_15040_gb300 import inputs
     exe = _compile(str(tmp_path))
-    xs = inputs.complex_input((batch,) + dims, 81, "normal", "c32")
+    dist = "normal" if dtype == "c32" else "uniform"
+    xs = np.ascontiguousarray(inputs.complex_input((batch,) + dims, 81, dist, dtype))
     fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     xs.tofile(fin)
-    r = subprocess.run([exe, fin, fout, str(direction), str(batch)] + [str(d) for d in dims],
+    r = subprocess.run([exe, fin, fout, str(CODES[dtype]), str(direction), str(batch)] + [str(d) for d in dims],
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
-    got = np.fromfile(fout, dtype=np.complex64).reshape(xs.shape).astype(np.complex128)
-    ref = oracle.fftn(xs.astype(np.complex128), rank=len(dims), sign=direction)
+    got = np.fromfile(fout, dtype=xs.dtype).reshape(xs.shape)
+    got = inputs.storage_to_c128(got, dtype)
+    # the library's default normalisation: paper for complex64, orthonormal for 16-bit storage
+    norm = oracle.NORM_PAPER if dtype == "c32" else oracle.NORM_ORTHO
+    ref = oracle.fftn(inputs.storage_to_c128(xs, dtype), rank=len(dims), sign=direction, norm=norm)
     err = oracle.rel_l2(got, ref)
-    print(f"C client {dims} x{batch} direction {direction}: rel_l2 {err:.2e}")
-    assert err < 5e-6
+    print(f"C client {dims} x{batch} {dtype} direction {direction}: rel_l2 {err:.2e}")
+    assert err < TOLS[dtype]
